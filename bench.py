@@ -1,0 +1,465 @@
+#!/usr/bin/env python3
+"""Throughput bench for GB300 bulk AES (one JSON line on rank 0).
+
+Default workload: AES-128 CTR encryption of one 1 GiB buffer of seeded
+uniform random bytes (the single-large-buffer case of the size sweep), data
+resident in HBM, one library call per step.  The input is larger than L2
+(129 MB), so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--bits 128|192|256] [--mode ctr|ecb_enc|ecb_dec] [--size-mib M]
+                  [--sweep] [--no-e2e] [--no-cpu] [--no-probes]
+
+Under torchrun (N > 1) every rank encrypts its own buffer (weak scaling, no
+data-path collective: the blocks are independent); the barrier and the
+max-over-ranks of the elapsed time are the only collectives.
+
+`--impl reference` times the CPU oracle (test infrastructure, the one other
+place this file runs it) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "AES-128/256 ECB/CTR GB/s on 1 GB300 vs roofline; batched-vs-plain; p50/p99"
+PAPER_BEST_GBPS = 6637e6 / 8 / 1e9  # Table I: 6637 Mb/s, pthreads on 32 cores (context only)
+SM_MAX_MHZ_FALLBACK = 2070.0
+HBM_FALLBACK_GBPS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--bits", type=int, default=128, choices=[128, 192, 256])
+    p.add_argument("--mode", default="ctr", choices=["ctr", "ecb_enc", "ecb_dec"])
+    p.add_argument("--size-mib", type=int, default=1024)
+    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--cta", type=int, default=0)
+    p.add_argument("--bpt", type=int, default=0)
+    p.add_argument("--sweep", action="store_true", help="also time the 36-run key/mode/size sweep")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-probes", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# environment: ranks, peaks, clocks
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", HBM_FALLBACK_GBPS), d.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK), "measured"
+    return HBM_FALLBACK_GBPS, SM_MAX_MHZ_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None,
+            "samples": len(sm),
+            "reasons": sorted(reasons),
+        }
+
+
+# ---------------------------------------------------------------------------
+# probes: the roofline's on-chip denominators
+# ---------------------------------------------------------------------------
+
+PROBE_NAMES = ["lop3", "prmt", "iadd", "shf", "imad", "lds32", "lop3+imad", "lop3+lds32",
+               "prmt+lds32", "lop3+prmt"]
+
+
+def run_probes() -> dict:
+    from paper_1403_7295_gb300 import build as B
+
+    L = ctypes.CDLL(B.PROBE_LIB_PATH)
+    L.aesgpu_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for kind, name in enumerate(PROBE_NAMES):
+        r, s = ctypes.c_double(), ctypes.c_double()
+        rc = L.aesgpu_probe_pipe(kind, 1024, 2000, ctypes.byref(r), ctypes.byref(s))
+        out[name] = round(r.value, 2) if rc == 0 else None
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+# Algorithmic table lookups per 16-byte block: one per state byte per round
+# (paper Fig. 1: Nr rounds of SubBytes over 16 bytes).
+def lookups_per_block(bits: int) -> int:
+    return 16 * {128: 10, 192: 12, 256: 14}[bits]
+
+
+def launch(A, mode, ks, iv, x, y, cfg, stream=None):
+    if mode == "ctr":
+        return A.aes_ctr_xcrypt(ks, iv, x, y, stream=stream, config=cfg)
+    if mode == "ecb_enc":
+        return A.aes_ecb_encrypt(ks, x, y, stream=stream, config=cfg)
+    return A.aes_ecb_decrypt(ks, x, y, stream=stream, config=cfg)
+
+
+def time_device(torch, fn, steps, warmup, barrier=None):
+    """CUDA-event time of `steps` calls of fn() on the current stream (ms total)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return e0.elapsed_time(e1)
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_1403_7295_gb300 import aes as A
+    from paper_1403_7295_gb300 import build as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    barrier = (lambda: dist.barrier()) if dist else None
+
+    B.build()
+    A.lib()
+    nbytes = args.size_mib << 20
+    seed = rank
+    bits = args.bits
+    key = synth.key_bytes(seed, bits)
+    iv = synth.iv_bytes(seed)
+    ks = A.aes_expand_key(key)
+    x = synth.bytes_torch(seed, synth.STREAM_DATA, nbytes, device="cuda")
+    y = torch.empty_like(x)
+    cfg = None
+    if args.variant or args.cta or args.bpt:
+        cfg = dict(variant=args.variant, cta_threads=args.cta, blocks_per_thread=args.bpt, grid_ctas=0)
+
+    hbm_peak, sm_max_mhz, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
+        gpu_id = "GPU-" + gpu_id
+
+    probes = run_probes() if (rank == 0 and not args.no_probes) else None
+
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), args.steps, args.warmup,
+                     barrier)
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    per_launch_s = ms / 1e3 / args.steps  # this rank's kernel, one launch per step
+    value = world * nbytes * args.steps / (ms_max / 1e3) / 1e9
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic: SplitMix64-seeded uniform random bytes, key and nonce per rank",
+        "config": {
+            "workload": f"AES-{bits} {args.mode.upper()} of one {args.size_mib} MiB buffer per GPU, "
+                        "device-resident (single-buffer sweep, largest-buffer headline case)",
+            "key_bits": bits, "mode": args.mode, "buffer_bytes": nbytes,
+            "l2": "input larger than L2 (129 MB); no flush",
+            "launch": cfg or "library default",
+            "parallelism": f"independent buffers x{world}",
+        },
+        "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        blocks = nbytes / 16
+        lk = lookups_per_block(bits) * blocks
+        g_lookups = lk / per_launch_s / 1e9
+        clock_mhz = sm_max_mhz
+        rl = {"bound": "alu", "unit": "Glookup/s", "achieved": round(g_lookups, 1),
+              "peak": None, "frac": None, "traffic": read_traffic(args),
+              "ops_per_block": lookups_per_block(bits),
+              "pipe": "32-bit shared-memory loads (replicated T-table lookups)",
+              "hbm_gbps_moved": round(2 * nbytes / per_launch_s / 1e9, 1),
+              "hbm_peak_gbps": hbm_peak, "hbm_frac": round(2 * nbytes / per_launch_s / 1e9 / hbm_peak, 4),
+              "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json copy bandwidth)" if peak_src == "measured"
+              else "fallback 6.8 TB/s"}
+        if probes and probes.get("lds32"):
+            peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
+            rl["peak"] = round(peak, 1)
+            rl["frac"] = round(g_lookups / peak, 4)
+            rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
+                                 f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
+        result["roofline"] = rl
+        result["probes_ops_per_clk_per_sm"] = probes
+        result["clocks"] = clocks
+        result["context"] = {"paper_best_cpu_gbps": round(PAPER_BEST_GBPS, 3),
+                             "paper_best_cpu": "6637 Mb/s, pthreads, 4x Xeon X7560 (Table I)"}
+        if not args.no_e2e:
+            result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
+        if args.sweep:
+            result["sweep"] = sweep(torch, A)
+        del x, y
+        torch.cuda.empty_cache()
+        if not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(args.bits, args.mode, budget_s=10.0)
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def read_traffic(args):
+    """dram bytes per launch from the committed ncu summary, if it still
+    matches the kernel source; else null."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ttable_ctr_aes128_1GiB.md")
+    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128:
+        return None
+    src = os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", "aes_ttable.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    per_gib = None
+    for ln in open(path):
+        if ln.startswith("traffic_bytes_per_GiB_launch:"):
+            parts = ln.split()
+            per_gib = float(parts[1])
+            if "source_sha256_16:" in parts and parts[parts.index("source_sha256_16:") + 1] != sha:
+                return None
+    if per_gib is None:
+        return None
+    return per_gib * (args.size_mib / 1024)
+
+
+def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):
+    """Same call with pinned HOST buffers: the kernel reads the input from
+    host memory and writes the result back to host memory (NVLink-C2C), so
+    both transfers are inside the timed call."""
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_in.copy_(synth.bytes_torch(0, synth.STREAM_DATA, nbytes, device="cuda").cpu())
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    steps = max(3, min(50, args.steps // 20))
+    ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, h_in, h_out, cfg), steps, 3)
+    val = nbytes * steps / (ms / 1e3) / 1e9
+    return {"value": round(val, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": steps,
+            "how": "aes call on pinned host input/output buffers (zero-copy over NVLink-C2C)"}
+
+
+def sweep(torch, A):
+    """The 36-run size sweep: {128,192,256} x {ECB,CTR} x {enc,dec} x {64 MiB, 1 GiB, 8 GiB}."""
+    out = []
+    run = 0
+    for size_mib in (64, 1024, 8192):
+        n = size_mib << 20
+        x = synth.bytes_torch(100 + size_mib, synth.STREAM_DATA, n, device="cuda")
+        y = torch.empty_like(x)
+        steps = max(5, int(2 * 2**30 / n * 10))
+        for bits in (128, 192, 256):
+            for mode in ("ecb_enc", "ecb_dec", "ctr_enc", "ctr_dec"):
+                ks = A.aes_expand_key(synth.key_bytes(run, bits))
+                iv = synth.iv_bytes(run)
+                m = "ctr" if mode.startswith("ctr") else mode
+                ms = time_device(torch, lambda: launch(A, m, ks, iv, x, y, None), steps, 3)
+                out.append({"bits": bits, "mode": mode, "size_mib": size_mib,
+                            "gbps": round(n * steps / (ms / 1e3) / 1e9, 1)})
+                run += 1
+        del x, y
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the oracle as it stands
+# ---------------------------------------------------------------------------
+
+def _oracle_call(o, bits, mode, key, iv, data, nthreads):
+    if mode == "ctr":
+        return o.ctr_xcrypt(key, bits, iv, data, nthreads=nthreads)
+    if mode == "ecb_enc":
+        return o.ecb_encrypt(key, bits, data, nthreads=nthreads)
+    return o.ecb_decrypt(key, bits, data, nthreads=nthreads)
+
+
+def cpu_baseline(bits, mode, budget_s=10.0) -> dict:
+    from oracle import Oracle
+
+    o = Oracle()
+    cores = os.cpu_count() or 1
+    key = synth.key_bytes(0, bits)
+    iv = synth.iv_bytes(0)
+    cal = synth.bytes_np(0, synth.STREAM_DATA, 1 << 20)
+    t0 = time.perf_counter()
+    _oracle_call(o, bits, mode, key, iv, cal, cores)
+    rate = (1 << 20) / max(time.perf_counter() - t0, 1e-6)
+    nbytes = int(max(1 << 20, min(1 << 30, rate * budget_s)) // (1 << 20)) << 20
+    data = synth.bytes_np(1, synth.STREAM_DATA, nbytes)
+    t0 = time.perf_counter()
+    _oracle_call(o, bits, mode, key, iv, data, cores)
+    dt = time.perf_counter() - t0
+    single = synth.bytes_np(2, synth.STREAM_DATA, 1 << 20)
+    t1 = time.perf_counter()
+    _oracle_call(o, bits, mode, key, iv, single, 0)
+    dt1 = time.perf_counter() - t1
+    return {"value": round(nbytes / dt / 1e9, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"AES-{bits} {mode} of {nbytes >> 20} MiB, pthreads over {cores} threads "
+                      "(the paper's contiguous chunk split)",
+            "single_thread_gbps": round((1 << 20) / dt1 / 1e9, 5)}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import Oracle
+
+    o = Oracle()
+    cores = os.cpu_count() or 1
+    bits, mode = args.bits, args.mode
+    key = synth.key_bytes(0, bits)
+    iv = synth.iv_bytes(0)
+    cal = synth.bytes_np(0, synth.STREAM_DATA, 1 << 20)
+    t0 = time.perf_counter()
+    _oracle_call(o, bits, mode, key, iv, cal, cores)
+    rate = (1 << 20) / max(time.perf_counter() - t0, 1e-6)
+    total_budget = 120.0  # seconds for warmup + steps
+    per_step = max(1 << 16, int(rate * total_budget / max(1, args.steps + args.warmup)) // 16 * 16)
+    per_step = min(per_step, 1 << 30)
+    data = synth.bytes_np(1, synth.STREAM_DATA, per_step)
+    for _ in range(args.warmup):
+        _oracle_call(o, bits, mode, key, iv, data, cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_call(o, bits, mode, key, iv, data, cores)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic: SplitMix64-seeded uniform random bytes",
+        "config": {"workload": f"AES-{bits} {mode.upper()} of one {args.size_mib} MiB buffer per GPU, "
+                               "device-resident (single-buffer sweep, largest-buffer headline case)",
+                   "key_bits": bits, "mode": mode, "buffer_bytes": args.size_mib << 20},
+        "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} bytes per step of the same workload, pthreads over {cores} threads"},
+        "e2e": {"value": round(value, 5), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,288 @@
+// aes_api.cu — the C ABI of libaesgpu.so: key expansion on the host, argument
+// validation, launch-shape choice and dispatch to the round kernels.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "aes_internal.h"
+#include "aes_tables.cuh"
+#include "aesgpu.h"
+
+namespace aesgpu {
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+aes_status cuda_failure(cudaError_t e) {
+  g_last_cuda_error = static_cast<int>(e);
+  return AES_ERR_CUDA;
+}
+
+constexpr const AesTables& H = kHostTables;
+
+uint32_t load_le32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+uint32_t sub_word(uint32_t w) {
+  return pack(H.sbox[w & 0xFF], H.sbox[(w >> 8) & 0xFF], H.sbox[(w >> 16) & 0xFF],
+              H.sbox[w >> 24]);
+}
+
+// InvMixColumns of one column word (FIPS-197 §5.3.3), for the equivalent
+// inverse cipher's schedule.
+uint32_t inv_mix_word(uint32_t w) {
+  const uint8_t a0 = w & 0xFF, a1 = (w >> 8) & 0xFF, a2 = (w >> 16) & 0xFF, a3 = w >> 24;
+  auto m = [](uint8_t a, uint8_t b) { return gf_mul(a, b); };
+  return pack(m(a0, 14) ^ m(a1, 11) ^ m(a2, 13) ^ m(a3, 9),
+              m(a0, 9) ^ m(a1, 14) ^ m(a2, 11) ^ m(a3, 13),
+              m(a0, 13) ^ m(a1, 9) ^ m(a2, 14) ^ m(a3, 11),
+              m(a0, 11) ^ m(a1, 13) ^ m(a2, 9) ^ m(a3, 14));
+}
+
+aes_status check_schedule(const aes_key_schedule* ks) {
+  if (ks == nullptr) return AES_ERR_ARG;
+  const bool ok = (ks->key_bits == 128 && ks->nr == 10) || (ks->key_bits == 192 && ks->nr == 12) ||
+                  (ks->key_bits == 256 && ks->nr == 14);
+  return ok ? AES_OK : AES_ERR_KEYSIZE;
+}
+
+// Resolve a caller pointer to one the current device can dereference.
+aes_status device_view(const void* p, const void** dev) {
+  cudaPointerAttributes attr{};
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) return cuda_failure(e);
+  int cur = 0;
+  e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_failure(e);
+  switch (attr.type) {
+    case cudaMemoryTypeDevice:
+      if (attr.device != cur) return AES_ERR_ARG;  // another GPU's memory
+      *dev = p;
+      return AES_OK;
+    case cudaMemoryTypeManaged:
+      *dev = p;
+      return AES_OK;
+    case cudaMemoryTypeHost:  // pinned host memory, mapped into the device's address space
+      if (attr.devicePointer == nullptr) return AES_ERR_ARG;
+      *dev = attr.devicePointer;
+      return AES_OK;
+    default:  // pageable host memory is not accepted by these calls
+      return AES_ERR_ARG;
+  }
+}
+
+aes_status check_buffers(const void* in, void* out, size_t nbytes, const void** din, void** dout) {
+  if (in == nullptr || out == nullptr) return AES_ERR_ARG;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+  if ((a | b) & 15u) return AES_ERR_ALIGN;
+  if (a != b && a < b + nbytes && b < a + nbytes) return AES_ERR_OVERLAP;
+  aes_status s = device_view(in, din);
+  if (s != AES_OK) return s;
+  const void* o = nullptr;
+  s = device_view(out, &o);
+  if (s != AES_OK) return s;
+  *dout = const_cast<void*>(o);
+  return AES_OK;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+// Default launch shapes (measured on GB300; see the bench's autotune output).
+struct Defaults {
+  int cta_threads, blocks_per_thread;
+};
+Defaults default_shape(Op op, int nr) {
+  (void)nr;
+  switch (op) {
+    case Op::kCtr: return {1024, 2};
+    case Op::kEcbEncrypt: return {1024, 2};
+    case Op::kEcbDecrypt: return {1024, 2};
+  }
+  return {1024, 2};
+}
+
+aes_status resolve_shape(Op op, int nr, uint64_t nblocks, const aes_launch_config* cfg,
+                         LaunchShape* shape) {
+  const Defaults d = default_shape(op, nr);
+  int variant = cfg ? cfg->variant : AES_VARIANT_AUTO;
+  if (variant != AES_VARIANT_AUTO && variant != AES_VARIANT_TTABLE) return AES_ERR_ARG;
+  int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : d.cta_threads;
+  int bpt = (cfg && cfg->blocks_per_thread) ? cfg->blocks_per_thread : d.blocks_per_thread;
+  if (cta < 128 || cta > 1024 || cta % 32 != 0) return AES_ERR_ARG;
+  if (bpt != 1 && bpt != 2 && bpt != 4) return AES_ERR_ARG;
+  int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
+  if (grid < 0) return AES_ERR_ARG;
+  // No more CTAs than there is work for (at least one, for a tail-only call).
+  const uint64_t per_cta = static_cast<uint64_t>(cta) * bpt;
+  const uint64_t needed = nblocks == 0 ? 1 : (nblocks + per_cta - 1) / per_cta;
+  if (static_cast<uint64_t>(grid) > needed) grid = static_cast<int>(needed);
+  *shape = LaunchShape{cta, bpt, grid};
+  return AES_OK;
+}
+
+void copy_round_keys(const uint32_t* src, int nr, RoundKeys* rk) {
+  std::memset(rk, 0, sizeof(*rk));
+  std::memcpy(rk->w, src, sizeof(uint32_t) * 4 * (nr + 1));
+}
+
+// Host-side T-table word: Ti[x] = te0[x] rotated left by 8i.
+uint32_t te(int i, uint32_t x) { return i == 0 ? H.te0[x] : rotl32(H.te0[x], 8 * i); }
+
+// CTR launch constants (see CtrParams): columns 0..2 of the state after the
+// initial AddRoundKey do not depend on the counter, so their contributions to
+// each round-1 column are summed here once.
+CtrParams make_ctr_params(const aes_key_schedule* ks, const uint8_t iv[16]) {
+  CtrParams cp{};
+  for (int c = 0; c < 4; ++c) cp.iv_w[c] = load_le32(iv + 4 * c);
+  cp.ctr0 = ((uint32_t)iv[12] << 24) | ((uint32_t)iv[13] << 16) | ((uint32_t)iv[14] << 8) | iv[15];
+  const uint32_t* rk = ks->rk_enc;
+  uint32_t s[3];
+  for (int c = 0; c < 3; ++c) s[c] = cp.iv_w[c] ^ rk[c];
+  cp.rk0w3 = rk[3];
+  for (int j = 0; j < 4; ++j) {
+    uint32_t acc = rk[4 + j];
+    for (int i = 0; i < 4; ++i) {
+      const int col = (j + i) & 3;  // ShiftRows: row i of output column j comes from column j+i
+      if (col == 3) continue;       // the counter column, looked up on the device
+      acc ^= te(i, (s[col] >> (8 * i)) & 0xFF);
+    }
+    cp.c1[j] = acc;
+  }
+  return cp;
+}
+
+aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void* in, void* out,
+               size_t nbytes, void* stream, const aes_launch_config* cfg) {
+  aes_status s = check_schedule(ks);
+  if (s != AES_OK) return s;
+  if (op == Op::kCtr && iv == nullptr) return AES_ERR_ARG;
+  if (op != Op::kCtr && nbytes % 16 != 0) return AES_ERR_LENGTH;
+  if (cfg && cfg->variant != AES_VARIANT_AUTO && cfg->variant != AES_VARIANT_TTABLE &&
+      cfg->variant != AES_VARIANT_BITSLICE)
+    return AES_ERR_ARG;
+  if (nbytes == 0) return AES_OK;
+  const void* din = nullptr;
+  void* dout = nullptr;
+  s = check_buffers(in, out, nbytes, &din, &dout);
+  if (s != AES_OK) return s;
+  const uint64_t nblocks = nbytes / 16;
+  const uint32_t tail = static_cast<uint32_t>(nbytes % 16);
+  LaunchShape shape{};
+  s = resolve_shape(op, static_cast<int>(ks->nr), nblocks, cfg, &shape);
+  if (s != AES_OK) return s;
+  RoundKeys rk;
+  copy_round_keys(op == Op::kEcbDecrypt ? ks->rk_dec : ks->rk_enc, static_cast<int>(ks->nr), &rk);
+  CtrParams cp{};
+  if (op == Op::kCtr) cp = make_ctr_params(ks, iv);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nr = static_cast<int>(ks->nr);
+  cudaError_t e = cudaSuccess;
+  switch (op) {
+    case Op::kEcbEncrypt: e = launch_ttable_enc(nr, din, dout, nblocks, 0, rk, cp, shape, st); break;
+    case Op::kEcbDecrypt: e = launch_ttable_dec(nr, din, dout, nblocks, 0, rk, cp, shape, st); break;
+    case Op::kCtr: e = launch_ttable_ctr(nr, din, dout, nblocks, tail, rk, cp, shape, st); break;
+  }
+  if (e != cudaSuccess) return cuda_failure(e);
+  return AES_OK;
+}
+
+}  // namespace
+}  // namespace aesgpu
+
+using namespace aesgpu;
+
+extern "C" {
+
+aes_status aes_expand_key(const uint8_t* key, int key_bits, aes_key_schedule* ks) {
+  if (key == nullptr || ks == nullptr) return AES_ERR_ARG;
+  int nk = 0;
+  switch (key_bits) {
+    case 128: nk = 4; break;
+    case 192: nk = 6; break;
+    case 256: nk = 8; break;
+    default: return AES_ERR_KEYSIZE;
+  }
+  std::memset(ks, 0, sizeof(*ks));
+  const int nr = nk + 6, nwords = 4 * (nr + 1);
+  ks->key_bits = static_cast<uint32_t>(key_bits);
+  ks->nr = static_cast<uint32_t>(nr);
+  uint32_t* w = ks->rk_enc;
+  for (int i = 0; i < nk; ++i) w[i] = load_le32(key + 4 * i);
+  uint8_t rcon = 1;
+  for (int i = nk; i < nwords; ++i) {
+    uint32_t t = w[i - 1];
+    if (i % nk == 0) {
+      t = sub_word((t >> 8) | (t << 24)) ^ rcon;  // RotWord on a little-endian word
+      rcon = gf_xtime(rcon);
+    } else if (nk == 8 && i % nk == 4) {
+      t = sub_word(t);
+    }
+    w[i] = w[i - nk] ^ t;
+  }
+  // Equivalent inverse cipher (FIPS-197 §5.3.5): reversed rounds, InvMixColumns
+  // on the middle ones.
+  for (int r = 0; r <= nr; ++r)
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t v = w[4 * (nr - r) + c];
+      ks->rk_dec[4 * r + c] = (r == 0 || r == nr) ? v : inv_mix_word(v);
+    }
+  return AES_OK;
+}
+
+aes_status aes_ecb_encrypt_ex(const aes_key_schedule* ks, const void* d_in, void* d_out,
+                              size_t nbytes, void* stream, const aes_launch_config* cfg) {
+  return run(Op::kEcbEncrypt, ks, nullptr, d_in, d_out, nbytes, stream, cfg);
+}
+
+aes_status aes_ecb_decrypt_ex(const aes_key_schedule* ks, const void* d_in, void* d_out,
+                              size_t nbytes, void* stream, const aes_launch_config* cfg) {
+  return run(Op::kEcbDecrypt, ks, nullptr, d_in, d_out, nbytes, stream, cfg);
+}
+
+aes_status aes_ctr_xcrypt_ex(const aes_key_schedule* ks, const uint8_t iv[16], const void* d_in,
+                             void* d_out, size_t nbytes, void* stream,
+                             const aes_launch_config* cfg) {
+  return run(Op::kCtr, ks, iv, d_in, d_out, nbytes, stream, cfg);
+}
+
+aes_status aes_ecb_encrypt(const aes_key_schedule* ks, const void* d_in, void* d_out,
+                           size_t nbytes, void* stream) {
+  return aes_ecb_encrypt_ex(ks, d_in, d_out, nbytes, stream, nullptr);
+}
+
+aes_status aes_ecb_decrypt(const aes_key_schedule* ks, const void* d_in, void* d_out,
+                           size_t nbytes, void* stream) {
+  return aes_ecb_decrypt_ex(ks, d_in, d_out, nbytes, stream, nullptr);
+}
+
+aes_status aes_ctr_xcrypt(const aes_key_schedule* ks, const uint8_t iv[16], const void* d_in,
+                          void* d_out, size_t nbytes, void* stream) {
+  return aes_ctr_xcrypt_ex(ks, iv, d_in, d_out, nbytes, stream, nullptr);
+}
+
+int aes_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* aes_status_string(aes_status s) {
+  switch (s) {
+    case AES_OK: return "ok";
+    case AES_ERR_ARG: return "invalid argument";
+    case AES_ERR_KEYSIZE: return "key size must be 128, 192 or 256 bits";
+    case AES_ERR_LENGTH: return "length must be a multiple of 16 bytes";
+    case AES_ERR_ALIGN: return "data pointers must be 16-byte aligned";
+    case AES_ERR_OVERLAP: return "input and output overlap";
+    case AES_ERR_PADDING: return "malformed PKCS#7 padding";
+    case AES_ERR_NOMEM: return "workspace too small";
+    case AES_ERR_CUDA: return "CUDA error";
+    case AES_ERR_TIMEOUT: return "device wait timed out";
+    case AES_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// aes_internal.h — launch interfaces between the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace aesgpu {
+
+enum class Op : int { kEcbEncrypt = 0, kEcbDecrypt = 1, kCtr = 2 };
+
+// Round keys travel in the kernel's parameter block (constant bank), so every
+// AddRoundKey reads a uniform constant operand.
+struct RoundKeys {
+  uint32_t w[60];
+};
+
+// CTR parameters, precomputed on the host per launch.  With the nonce fixed,
+// columns 0..2 of the state after the initial AddRoundKey are the same for
+// every block, so 12 of the 16 first-round lookups are folded into c1[]:
+//   round-1 column j = c1[j] ^ T_{3-j}[byte 3-j of (counter word ^ rk0w3)].
+struct CtrParams {
+  uint32_t ctr0;    // counter value of block 0 of this launch
+  uint32_t rk0w3;   // round-0 key word 3
+  uint32_t c1[4];   // folded round-1 columns (round-1 key included)
+  uint32_t iv_w[4]; // IV words (little-endian), used by the partial tail block
+};
+
+struct LaunchShape {
+  int cta_threads;
+  int blocks_per_thread;
+  int grid_ctas;
+};
+
+// T-table launches, one per operation (each returns the launch's CUDA error).
+#define AESGPU_DECLARE_LAUNCH(name)                                                          \
+  cudaError_t name(int nr, const void* in, void* out, uint64_t nblocks, uint32_t tail_bytes, \
+                   const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,        \
+                   cudaStream_t stream);
+AESGPU_DECLARE_LAUNCH(launch_ttable_enc)
+AESGPU_DECLARE_LAUNCH(launch_ttable_dec)
+AESGPU_DECLARE_LAUNCH(launch_ttable_ctr)
+#undef AESGPU_DECLARE_LAUNCH
+
+// Dynamic shared memory of the T-table kernels (bytes).
+constexpr int kTtableSmemEnc = 128 * 1024;
+constexpr int kTtableSmemDec = 192 * 1024;
+
+}  // namespace aesgpu

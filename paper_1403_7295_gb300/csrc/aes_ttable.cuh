@@ -1,0 +1,250 @@
+// aes_ttable.cuh — single-buffer AES kernels, T-table round variant.
+//
+// One 16-byte AES block per thread-iteration, held as four 32-bit column words
+// (little-endian: byte r of column c is state row r, FIPS-197 §3.4).  A full
+// round (paper Fig. 1 step 3: SubBytes, ShiftRows, MixColumns, AddRoundKey)
+// is, per output column j,
+//   t_j = T0[s_j.b0] ^ T1[s_{j+1}.b1] ^ T2[s_{j+2}.b2] ^ T3[s_{j+3}.b3] ^ rk_j
+// where Ti = te0 rotated left by 8i bits; ShiftRows is the choice of source
+// column and MixColumns is folded into the table words.  The final round
+// (Fig. 1 step 4) picks the plain S-box byte out of the same words.
+// Decryption uses the equivalent inverse cipher (FIPS-197 §5.3.5): td0 tables
+// with the source columns shifted the other way, and the inverse S-box.
+//
+// Tables live in shared memory, replicated once per lane: row x of a table is
+// 32 copies of the word, so lane l always reads bank l and a warp's 32
+// lookups never conflict.  One PRMT builds a lookup address: the state byte
+// goes to bits 8..15 (row x at x*256 bytes) and the lane's byte offset to
+// bits 0..7.  Two tables share each 256-byte row (lanes at +0 and +128).
+//
+// Launch: a persistent grid (one CTA per SM by default; the tables take
+// 128 KiB, 192 KiB for decryption), grid-stride over blocks, `BPT` blocks per
+// thread per iteration for instruction-level parallelism, 128-bit streaming
+// loads and stores that coalesce across the warp.
+#pragma once
+#include "aes_internal.h"
+#include "aes_tables.cuh"
+
+namespace aesgpu {
+namespace {
+
+__device__ const AesTables kDevTables = make_tables();
+
+constexpr uint32_t kRegionB = 64 * 1024;   // te2|te3 (td2|td3)
+constexpr uint32_t kRegionC = 128 * 1024;  // is4 (decryption only)
+
+__device__ __forceinline__ uint32_t rotl(uint32_t v, int k) { return __funnelshift_l(v, v, k); }
+
+// Shared-memory lookups.  a/b/c are the region bases; lo = lane*4 selects the
+// first table of a row, hi = lane*4 + 128 the second.
+struct Tabs {
+  const char* a;
+  const char* b;
+  const char* c;
+  uint32_t lo, hi;
+  // word at base + (byte k of x) * 256 + lane offset; sel = 0x55k4
+  __device__ __forceinline__ uint32_t ld(const char* base, uint32_t x, uint32_t lane_off,
+                                         uint32_t sel) const {
+    return *reinterpret_cast<const uint32_t*>(base + __byte_perm(x, lane_off, sel));
+  }
+  // Ti[byte i of x]
+  __device__ __forceinline__ uint32_t t0(uint32_t x) const { return ld(a, x, lo, 0x5504); }
+  __device__ __forceinline__ uint32_t t1(uint32_t x) const { return ld(a, x, hi, 0x5514); }
+  __device__ __forceinline__ uint32_t t2(uint32_t x) const { return ld(b, x, lo, 0x5524); }
+  __device__ __forceinline__ uint32_t t3(uint32_t x) const { return ld(b, x, hi, 0x5534); }
+};
+
+// Byte 0 of a, byte 1 of b, byte 2 of c, byte 3 of d.
+__device__ __forceinline__ uint32_t merge_bytes(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  return __byte_perm(__byte_perm(a, b, 0x0050), __byte_perm(c, d, 0x7200), 0x7610);
+}
+
+struct State {
+  uint32_t s0, s1, s2, s3;
+};
+
+__device__ __forceinline__ void enc_round(const Tabs& T, State& s, const uint32_t* k) {
+  const uint32_t t0 = T.t0(s.s0) ^ T.t1(s.s1) ^ T.t2(s.s2) ^ T.t3(s.s3) ^ k[0];
+  const uint32_t t1 = T.t0(s.s1) ^ T.t1(s.s2) ^ T.t2(s.s3) ^ T.t3(s.s0) ^ k[1];
+  const uint32_t t2 = T.t0(s.s2) ^ T.t1(s.s3) ^ T.t2(s.s0) ^ T.t3(s.s1) ^ k[2];
+  const uint32_t t3 = T.t0(s.s3) ^ T.t1(s.s0) ^ T.t2(s.s1) ^ T.t3(s.s2) ^ k[3];
+  s = State{t0, t1, t2, t3};
+}
+
+// Final encryption round: S(x) is byte 0 of te2, byte 1 of te3, byte 2 of
+// te0 and byte 3 of te1, so column j is assembled from those four lookups.
+__device__ __forceinline__ uint32_t enc_final_col(const Tabs& T, uint32_t a, uint32_t b,
+                                                  uint32_t c, uint32_t d, uint32_t k) {
+  return merge_bytes(T.ld(T.b, a, T.lo, 0x5504), T.ld(T.b, b, T.hi, 0x5514),
+                     T.ld(T.a, c, T.lo, 0x5524), T.ld(T.a, d, T.hi, 0x5534)) ^ k;
+}
+
+__device__ __forceinline__ void enc_final(const Tabs& T, State& s, const uint32_t* k) {
+  const uint32_t f0 = enc_final_col(T, s.s0, s.s1, s.s2, s.s3, k[0]);
+  const uint32_t f1 = enc_final_col(T, s.s1, s.s2, s.s3, s.s0, k[1]);
+  const uint32_t f2 = enc_final_col(T, s.s2, s.s3, s.s0, s.s1, k[2]);
+  const uint32_t f3 = enc_final_col(T, s.s3, s.s0, s.s1, s.s2, k[3]);
+  s = State{f0, f1, f2, f3};
+}
+
+// Inverse round: InvShiftRows takes row r of column j from column j - r.
+__device__ __forceinline__ void dec_round(const Tabs& T, State& s, const uint32_t* k) {
+  const uint32_t t0 = T.t0(s.s0) ^ T.t1(s.s3) ^ T.t2(s.s2) ^ T.t3(s.s1) ^ k[0];
+  const uint32_t t1 = T.t0(s.s1) ^ T.t1(s.s0) ^ T.t2(s.s3) ^ T.t3(s.s2) ^ k[1];
+  const uint32_t t2 = T.t0(s.s2) ^ T.t1(s.s1) ^ T.t2(s.s0) ^ T.t3(s.s3) ^ k[2];
+  const uint32_t t3 = T.t0(s.s3) ^ T.t1(s.s2) ^ T.t2(s.s1) ^ T.t3(s.s0) ^ k[3];
+  s = State{t0, t1, t2, t3};
+}
+
+__device__ __forceinline__ uint32_t dec_final_col(const Tabs& T, uint32_t a, uint32_t b,
+                                                  uint32_t c, uint32_t d, uint32_t k) {
+  return merge_bytes(T.ld(T.c, a, T.lo, 0x5504), T.ld(T.c, b, T.lo, 0x5514),
+                     T.ld(T.c, c, T.lo, 0x5524), T.ld(T.c, d, T.lo, 0x5534)) ^ k;
+}
+
+__device__ __forceinline__ void dec_final(const Tabs& T, State& s, const uint32_t* k) {
+  const uint32_t f0 = dec_final_col(T, s.s0, s.s3, s.s2, s.s1, k[0]);
+  const uint32_t f1 = dec_final_col(T, s.s1, s.s0, s.s3, s.s2, k[1]);
+  const uint32_t f2 = dec_final_col(T, s.s2, s.s1, s.s0, s.s3, k[2]);
+  const uint32_t f3 = dec_final_col(T, s.s3, s.s2, s.s1, s.s0, k[3]);
+  s = State{f0, f1, f2, f3};
+}
+
+// Fill the replicated tables; warp w writes rows w, w + nwarps, ...
+template <bool kDec>
+__device__ __forceinline__ void fill_tables(uint32_t* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int x = warp; x < 256; x += nwarps) {
+    const uint32_t v = kDec ? kDevTables.td0[x] : kDevTables.te0[x];
+    uint32_t* ra = sm + x * 64;
+    uint32_t* rb = sm + kRegionB / 4 + x * 64;
+    ra[lane] = v;
+    ra[32 + lane] = rotl(v, 8);
+    rb[lane] = rotl(v, 16);
+    rb[32 + lane] = rotl(v, 24);
+    if (kDec) sm[kRegionC / 4 + x * 64 + lane] = kDevTables.is4[x];
+  }
+}
+
+// Full cipher of one block whose state already had round key 0 added.
+template <int NR>
+__device__ __forceinline__ void encrypt_rounds(const Tabs& T, State& s, const RoundKeys& rk,
+                                               int first_round) {
+#pragma unroll
+  for (int r = 1; r < NR; ++r)
+    if (r >= first_round) enc_round(T, s, &rk.w[4 * r]);
+  enc_final(T, s, &rk.w[4 * NR]);
+}
+
+// CTR keystream of block `idx` (see CtrParams: round 1 is partly folded).
+template <int NR>
+__device__ __forceinline__ State ctr_keystream(const Tabs& T, const RoundKeys& rk,
+                                               const CtrParams& cp, uint64_t idx) {
+  const uint32_t ctr = cp.ctr0 + static_cast<uint32_t>(idx);  // modulo 2^32
+  const uint32_t x = __byte_perm(ctr, 0, 0x0123) ^ cp.rk0w3;  // big-endian counter word
+  State s{cp.c1[0] ^ T.t3(x), cp.c1[1] ^ T.t2(x), cp.c1[2] ^ T.t1(x), cp.c1[3] ^ T.t0(x)};
+  encrypt_rounds<NR>(T, s, rk, 2);
+  return s;
+}
+
+__device__ __forceinline__ uint4 xor4(uint4 v, const State& s) {
+  return make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3);
+}
+
+template <Op OP, int NR, int BPT>
+__global__ void __launch_bounds__(1024, 1)
+    ttable_kernel(const uint4* in, uint4* out, uint64_t nblocks, uint32_t tail_bytes,
+                  const __grid_constant__ RoundKeys rk, const __grid_constant__ CtrParams cp) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  constexpr bool kDec = (OP == Op::kEcbDecrypt);
+  fill_tables<kDec>(smem);
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31;
+  const char* base = reinterpret_cast<const char*>(smem);
+  const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
+
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x * BPT;
+  for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x * BPT + threadIdx.x;
+       i0 < nblocks; i0 += stride) {
+    uint4 v[BPT];
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+      const uint64_t idx = i0 + static_cast<uint64_t>(k) * blockDim.x;
+      v[k] = idx < nblocks ? __ldcs(in + idx) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+      const uint64_t idx = i0 + static_cast<uint64_t>(k) * blockDim.x;
+      uint4 r;
+      if constexpr (OP == Op::kCtr) {
+        r = xor4(v[k], ctr_keystream<NR>(T, rk, cp, idx));
+      } else if constexpr (OP == Op::kEcbEncrypt) {
+        State s{v[k].x ^ rk.w[0], v[k].y ^ rk.w[1], v[k].z ^ rk.w[2], v[k].w ^ rk.w[3]};
+        encrypt_rounds<NR>(T, s, rk, 1);
+        r = make_uint4(s.s0, s.s1, s.s2, s.s3);
+      } else {
+        State s{v[k].x ^ rk.w[0], v[k].y ^ rk.w[1], v[k].z ^ rk.w[2], v[k].w ^ rk.w[3]};
+#pragma unroll
+        for (int rr = 1; rr < NR; ++rr) dec_round(T, s, &rk.w[4 * rr]);
+        dec_final(T, s, &rk.w[4 * NR]);
+        r = make_uint4(s.s0, s.s1, s.s2, s.s3);
+      }
+      if (idx < nblocks) __stcs(out + idx, r);
+    }
+  }
+
+  // CTR partial last block: its leading keystream bytes, one thread.
+  if constexpr (OP == Op::kCtr) {
+    if (tail_bytes != 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+      const State s = ctr_keystream<NR>(T, rk, cp, nblocks);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
+      uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
+      for (uint32_t b = 0; b < tail_bytes; ++b) {
+        const uint32_t w = b < 4 ? s.s0 : b < 8 ? s.s1 : b < 12 ? s.s2 : s.s3;
+        dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
+      }
+    }
+  }
+}
+
+template <Op OP, int NR, int BPT>
+cudaError_t launch_one(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                       const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                       cudaStream_t stream) {
+  auto kern = ttable_kernel<OP, NR, BPT>;
+  const int smem = OP == Op::kEcbDecrypt ? kTtableSmemDec : kTtableSmemEnc;
+  // Opt in to the large dynamic shared-memory carve-out (idempotent, host-only).
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<shape.grid_ctas, shape.cta_threads, smem, stream>>>(
+      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
+  return cudaGetLastError();
+}
+
+template <Op OP, int NR>
+cudaError_t dispatch_bpt(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                         const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                         cudaStream_t stream) {
+  switch (shape.blocks_per_thread) {
+    case 1: return launch_one<OP, NR, 1>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 2: return launch_one<OP, NR, 2>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 4: return launch_one<OP, NR, 4>(in, out, nblocks, tail, rk, cp, shape, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <Op OP>
+inline cudaError_t dispatch_nr(int nr, const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                        const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                        cudaStream_t stream) {
+  switch (nr) {
+    case 10: return dispatch_bpt<OP, 10>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 12: return dispatch_bpt<OP, 12>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 14: return dispatch_bpt<OP, 14>(in, out, nblocks, tail, rk, cp, shape, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace aesgpu

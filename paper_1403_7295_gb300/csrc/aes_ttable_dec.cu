@@ -1,0 +1,12 @@
+// aes_ttable_dec.cu — instantiates the T-table kernels for Op::kEcbDecrypt.
+#include "aes_ttable.cuh"
+
+namespace aesgpu {
+
+cudaError_t launch_ttable_dec(int nr, const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                            const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                            cudaStream_t stream) {
+  return dispatch_nr<Op::kEcbDecrypt>(nr, in, out, nblocks, tail, rk, cp, shape, stream);
+}
+
+}  // namespace aesgpu

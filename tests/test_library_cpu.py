@@ -1,0 +1,122 @@
+"""Host-side checks of libaesgpu.so that need no GPU.
+
+* the library builds for sm_103a, loads, and exports every entry point that
+  include/*.h declares;
+* host key expansion equals the oracle's (FIPS-197 §5.2), and the decryption
+  schedule is the equivalent inverse cipher's (§5.3.5);
+* argument validation that happens before any CUDA call returns the
+  documented status codes.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from paper_1403_7295_gb300 import aes as A
+from paper_1403_7295_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return A.lib()
+
+
+def declared_entry_points(header="aesgpu.h"):
+    names = set()
+    for h in [os.path.join(ROOT, "include", header)]:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(aes\w*)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    headers = sorted(os.path.basename(h) for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    assert headers == ["aesgpu.h", "aesgpu_probe.h"]
+    names = declared_entry_points("aesgpu.h")
+    assert "aes_ctr_xcrypt" in names and "aes_expand_key" in names
+    for n in names:
+        assert hasattr(lib, n), f"libaesgpu.so does not export {n}"
+    probe = ctypes.CDLL(B.PROBE_LIB_PATH)
+    pnames = declared_entry_points("aesgpu_probe.h")
+    assert "aesgpu_probe_pipe" in pnames
+    for n in pnames:
+        assert hasattr(probe, n), f"libaesgpu_probe.so does not export {n}"
+
+
+def test_build_targets_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+    assert os.path.dirname(B.LIB_PATH).startswith(ROOT), "the library is built in-tree"
+
+
+@pytest.mark.parametrize("bits", [128, 192, 256])
+def test_expand_key_matches_oracle(lib, oracle, bits):
+    for seed in range(10):
+        key = synth.key_bytes(100 + seed, bits)
+        ks = A.aes_expand_key(key, bits)
+        w, nr = oracle.key_expansion(key, bits)
+        assert ks.nr == nr and ks.key_bits == bits
+        nwords = 4 * (nr + 1)
+        enc = np.array(ks.rk_enc[:nwords], dtype="<u4").view(np.uint8)
+        assert np.array_equal(enc, w)
+        assert all(v == 0 for v in ks.rk_enc[nwords:])
+        # equivalent inverse cipher: round r uses InvMixColumns(round key nr - r)
+        dec = np.array(ks.rk_dec[:nwords], dtype="<u4").view(np.uint8).reshape(nr + 1, 4, 4)
+        rounds = w.reshape(nr + 1, 4, 4)
+        for r in range(nr + 1):
+            src = rounds[nr - r]
+            want = src if r in (0, nr) else np.stack([oracle.inv_mix_column(c) for c in src])
+            assert np.array_equal(dec[r], want), (seed, r)
+
+
+def test_expand_key_rejects_bad_sizes(lib):
+    for bits in (0, 64, 129, 512):
+        with pytest.raises(A.AesError) as e:
+            A.aes_expand_key(np.zeros(64, np.uint8), bits)
+        assert e.value.status == 2
+    ks = A.KeySchedule()
+    assert lib.aes_expand_key(None, 128, ctypes.byref(ks)) == 1
+
+
+def _call(lib, fn, ks, inp, out, n, iv=None, cfg=None):
+    if fn == "ctr":
+        ivb = (ctypes.c_uint8 * 16)() if iv is None else iv
+        return lib.aes_ctr_xcrypt_ex(ctypes.byref(ks) if ks is not None else None, ivb, inp, out, n,
+                                     None, cfg)
+    f = lib.aes_ecb_encrypt_ex if fn == "enc" else lib.aes_ecb_decrypt_ex
+    return f(ctypes.byref(ks) if ks is not None else None, inp, out, n, None, cfg)
+
+
+def test_validation_before_any_cuda_call(lib):
+    ks = A.aes_expand_key(synth.key_bytes(0, 128))
+    base = 1 << 20  # never dereferenced: every case below fails validation first
+    for fn in ("enc", "dec", "ctr"):
+        assert _call(lib, fn, None, base, base, 16) == 1            # null schedule
+        bad = A.KeySchedule()
+        ctypes.memmove(ctypes.byref(bad), ctypes.byref(ks), ctypes.sizeof(ks))
+        bad.nr = 11
+        assert _call(lib, fn, bad, base, base, 16) == 2             # inconsistent schedule
+        assert _call(lib, fn, ks, 0, base, 16) == 1                 # null input
+        assert _call(lib, fn, ks, base + 8, base + 4096, 32) == 4   # misaligned
+        assert _call(lib, fn, ks, base, base + 16, 64) == 5         # partial overlap
+        assert _call(lib, fn, ks, base, base + 16, 0) == 0          # empty is a no-op
+        cfg = A.LaunchConfig(variant=7)
+        assert _call(lib, fn, ks, base, base + 4096, 16, cfg=ctypes.byref(cfg)) == 1
+    assert _call(lib, "enc", ks, base, base + 4096, 17) == 3        # ECB needs whole blocks
+    assert _call(lib, "dec", ks, base, base + 4096, 8) == 3
+    assert lib.aes_ctr_xcrypt(ctypes.byref(ks), None, base, base, 16, None) == 1  # null IV
+
+
+def test_status_strings(lib):
+    for s in range(11):
+        assert lib.aes_status_string(s)
+    assert lib.aes_status_string(99) == b"unknown status"
