@@ -108,7 +108,8 @@ def _stream_handle(stream, tensor):
     import torch
 
     if stream is None:
-        stream = torch.cuda.current_stream(tensor.device)
+        # host (pinned) tensors run on the current device's stream
+        stream = torch.cuda.current_stream(tensor.device if tensor.is_cuda else None)
     return ctypes.c_void_p(stream.cuda_stream)
 
 
