@@ -58,6 +58,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-probes", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-message workloads")
     return p.parse_args()
 
 
@@ -304,6 +305,11 @@ def gpu_arm(args):
             result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
         if args.sweep:
             result["sweep"] = sweep(torch, A)
+        if not args.no_batch:
+            del x, y
+            torch.cuda.empty_cache()
+            x = y = None
+            result["batched"] = batched_arm(torch, A, value if world == 1 else None)
         del x, y
         torch.cuda.empty_cache()
         if not args.no_cpu:
@@ -349,6 +355,89 @@ def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):
     return {"value": round(val, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "steps": steps,
             "how": "aes call on pinned host input/output buffers (zero-copy over NVLink-C2C)"}
+
+
+def time_graph(torch, b, steps):
+    """CUDA-event time (ms) of `steps` replays of a captured batch graph."""
+    return time_device(torch, b.replay, steps, 3)
+
+
+def batched_arm(torch, A, ctr128_gbps):
+    """Batched workloads: (a) 16,384 messages, log-uniform 64 B .. 4 MiB, mixed
+    key sizes, CTR, one persistent launch in a CUDA graph with an autotuned
+    shape, against the byte-weighted harmonic mix of single-buffer 1 GiB CTR
+    rates; (b) 1,000,000 packet-sized AES-128 CTR messages with keys expanded
+    on the device vs pre-expanded schedules."""
+    from paper_1403_7295_gb300 import batch as B
+    from synth import workloads as W
+
+    out = {}
+    # single-buffer 1 GiB CTR rates per key size (128 from the headline run)
+    rates = {}
+    n = 1 << 30
+    x = synth.bytes_torch(7, synth.STREAM_DATA, n, device="cuda")
+    y = torch.empty_like(x)
+    for bits in (128, 192, 256):
+        if bits == 128 and ctr128_gbps:
+            rates[bits] = ctr128_gbps
+            continue
+        ks = A.aes_expand_key(synth.key_bytes(7, bits))
+        iv = synth.iv_bytes(7)
+        ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y), 100, 5)
+        rates[bits] = n * 100 / (ms / 1e3) / 1e9
+    del x, y
+    torch.cuda.empty_cache()
+
+    wl = W.batched_varlen(3, 16384)
+    lengths, kb = wl["lengths"], wl["key_bits"]
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(3, synth.STREAM_DATA, total, device="cuda")
+    b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=kb, ivs=wl["ivs"])
+    cfg = B.autotune(b)
+    b.capture(cfg)
+    steps = 50
+    ms = time_graph(torch, b, steps)
+    nbytes = b.total_input_bytes()
+    gbps = nbytes * steps / (ms / 1e3) / 1e9
+    by_bits = {bits: float(lengths[kb == bits].sum()) for bits in (128, 192, 256)}
+    mix = sum(by_bits.values()) / sum(by_bits[k] / rates[k] for k in by_bits)
+    out["varlen_16384"] = {
+        "gbps": round(gbps, 1), "bytes": nbytes, "ms_per_batch": round(ms / steps, 3),
+        "plain_ctr_1GiB_gbps": {str(k): round(v, 1) for k, v in rates.items()},
+        "plain_mix_gbps": round(mix, 1), "ratio_vs_plain": round(gbps / mix, 4),
+        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
+        "kernels_per_batch": 4, "graph": True,
+    }
+    del b, data
+    torch.cuda.empty_cache()
+
+    wl = W.small_messages(4, 1_000_000)
+    lengths = wl["lengths"]
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(4, synth.STREAM_DATA, total, device="cuda")
+    b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=wl["key_bits"], ivs=wl["ivs"])
+    cfg = B.autotune(b)
+    b.capture(cfg)
+    ms_dev = time_graph(torch, b, steps)
+    nbytes = b.total_input_bytes()
+    # the same batch with pre-expanded schedules (one per message)
+    table = bytearray()
+    keys = wl["keys"]
+    for m in range(b.n):
+        table += bytes(A.aes_expand_key(keys[m][:16], 128))
+    sched = torch.frombuffer(table, dtype=torch.uint8).cuda()
+    b2 = B.Batch(B.BATCH_CTR, data, in_off, lengths, schedules=sched, n_schedules=b.n,
+                 sched_idx=np.arange(b.n, dtype=np.uint32), ivs=wl["ivs"], out=b.out)
+    b2.capture(cfg)
+    ms_pre = time_graph(torch, b2, steps)
+    out["small_1M"] = {
+        "gbps_device_key_expansion": round(nbytes * steps / (ms_dev / 1e3) / 1e9, 1),
+        "gbps_preexpanded": round(nbytes * steps / (ms_pre / 1e3) / 1e9, 1),
+        "bytes": nbytes, "ms_per_batch_device_keys": round(ms_dev / steps, 3),
+        "ms_per_batch_preexpanded": round(ms_pre / steps, 3),
+        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
+    }
+    return out
 
 
 def sweep(torch, A):

@@ -115,6 +115,80 @@ aes_status aes_ctr_xcrypt_ex(const aes_key_schedule *ks, const uint8_t iv[16], c
                              void *d_out, size_t nbytes, void *stream,
                              const aes_launch_config *cfg);
 
+/* ---- Batched messages (one persistent launch) --------------------------
+ *
+ * Many independent messages of uneven byte lengths, each with its own key
+ * and IV, processed by one call: the paper's chunk-per-thread scheme (§IV.B)
+ * with chunks = messages.  A device prefix sum over per-message block
+ * counts maps 16-byte blocks to messages; a persistent kernel claims tiles
+ * of blocks, expands each message's key on the device (FIPS-197 §5.2) and
+ * runs the same rounds as the single-buffer calls.  One operation per call:
+ *   AES_BATCH_CTR              CTR (SP 800-38A §6.5), any length; output
+ *                              length = input length.
+ *   AES_BATCH_ECB_PKCS7_ENCRYPT  PKCS#7-pad (1..16 bytes) then ECB;
+ *                              output length = 16*floor(len/16) + 16.
+ *   AES_BATCH_ECB_PKCS7_DECRYPT  ECB-decrypt (len a positive multiple of
+ *                              16), check the padding; the whole padded
+ *                              plaintext is written and out_len gives the
+ *                              unpadded length.
+ */
+typedef enum aes_batch_op {
+    AES_BATCH_CTR = 0,
+    AES_BATCH_ECB_PKCS7_ENCRYPT = 1,
+    AES_BATCH_ECB_PKCS7_DECRYPT = 2
+} aes_batch_op;
+
+/* Description of one batch.  The struct itself is read on the host during
+ * the call; every array it points to is device memory, owned by the caller,
+ * and must stay valid until the stream has executed the work. */
+typedef struct aes_batch {
+    uint32_t n_msgs;
+    uint32_t op;                  /* aes_batch_op */
+    const uint8_t *in;            /* input arena (device) */
+    uint8_t *out;                 /* output arena (device); outputs must not overlap inputs
+                                     of other messages or each other (in == out per message is
+                                     allowed for CTR) */
+    const uint64_t *in_off;       /* [n_msgs] byte offset of message m in `in`, multiple of 16 */
+    const uint64_t *in_len;       /* [n_msgs] byte length of message m */
+    const uint64_t *out_off;      /* [n_msgs] byte offset of m's output in `out`, multiple of 16 */
+    /* Key source: raw keys expanded on the device, or pre-expanded schedules. */
+    const uint8_t *keys;          /* [n_msgs][32] raw keys (first key_bits/8 bytes used), 16-B aligned, or NULL */
+    const uint32_t *key_bits;     /* [n_msgs] 128, 192 or 256 (with keys) */
+    const aes_key_schedule *schedules; /* [n_schedules] device table (when keys == NULL) */
+    const uint32_t *sched_idx;    /* [n_msgs] index into schedules */
+    uint32_t n_schedules;
+    uint32_t reserved;
+    const uint8_t *iv;            /* [n_msgs][16] IVs, 16-B aligned (CTR only; else NULL) */
+    uint64_t *out_len;            /* [n_msgs] out: output bytes per message (may be NULL) */
+    int32_t *status;              /* [n_msgs] out: aes_status per message (may be NULL) */
+} aes_batch;
+
+/* Optional launch shape of the persistent kernel; zero fields = default. */
+typedef struct aes_batch_config {
+    int32_t cta_threads;  /* 256..1024, multiple of 32 */
+    int32_t tile_blocks;  /* 16-byte blocks a CTA claims at a time: multiple of cta_threads, <= 65536 */
+    int32_t grid_ctas;    /* 0 = one per SM */
+    int32_t reserved;
+} aes_batch_config;
+
+/* Bytes of device workspace aes_batch_submit needs for n_msgs messages. */
+size_t aes_batch_workspace_size(uint32_t n_msgs);
+
+/* Enqueue one batch on `stream` (4 kernel launches: count+scan, chunk scan,
+ * offset fix, persistent cipher kernel; no allocation, no host sync, so the
+ * call can be captured into a CUDA graph and replayed).  d_workspace: device,
+ * 256-byte aligned, at least aes_batch_workspace_size(n_msgs) bytes; its
+ * contents need no initialisation.  Per-message failures (bad key size,
+ * unaligned offset, bad ECB length or padding) are reported in status[m]
+ * with zero output bytes; the rest of the batch proceeds.  Returns
+ * AES_ERR_ARG for missing arrays or an unknown op, AES_ERR_NOMEM for a
+ * short workspace, AES_ERR_ALIGN for a misaligned arena, key or IV base.
+ * Messages are not checked against each other for overlap. */
+aes_status aes_batch_submit(const aes_batch *b, void *d_workspace, size_t workspace_bytes,
+                            void *stream);
+aes_status aes_batch_submit_ex(const aes_batch *b, void *d_workspace, size_t workspace_bytes,
+                               void *stream, const aes_batch_config *cfg);
+
 /* The CUDA error code behind the calling thread's last AES_ERR_CUDA (0 if none). */
 int aes_last_cuda_error(void);
 

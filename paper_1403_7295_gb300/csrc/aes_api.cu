@@ -4,6 +4,7 @@
 
 #include <cstring>
 
+#include "aes_batch.h"
 #include "aes_internal.h"
 #include "aes_tables.cuh"
 #include "aesgpu.h"
@@ -192,6 +193,62 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
   return AES_OK;
 }
 
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* stream,
+                        const aes_batch_config* cfg) {
+  if (b == nullptr) return AES_ERR_ARG;
+  if (b->op > AES_BATCH_ECB_PKCS7_DECRYPT) return AES_ERR_ARG;
+  if (b->n_msgs == 0) return AES_OK;
+  if (!b->in || !b->out || !b->in_off || !b->in_len || !b->out_off) return AES_ERR_ARG;
+  const bool raw_keys = b->keys != nullptr;
+  if (raw_keys ? b->key_bits == nullptr
+               : (b->schedules == nullptr || b->sched_idx == nullptr || b->n_schedules == 0))
+    return AES_ERR_ARG;
+  if (b->op == AES_BATCH_CTR && b->iv == nullptr) return AES_ERR_ARG;
+  if (ws == nullptr) return AES_ERR_ARG;
+  if (!aligned(b->in, 16) || !aligned(b->out, 16) || !aligned(ws, 256)) return AES_ERR_ALIGN;
+  if (raw_keys && !aligned(b->keys, 16)) return AES_ERR_ALIGN;
+  if (!raw_keys && !aligned(b->schedules, 4)) return AES_ERR_ALIGN;
+  if (b->iv && !aligned(b->iv, 16)) return AES_ERR_ALIGN;
+  if (ws_bytes < batch_workspace_bytes(b->n_msgs)) return AES_ERR_NOMEM;
+  int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : 1024;
+  int tile = (cfg && cfg->tile_blocks) ? cfg->tile_blocks : 8192;
+  int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
+  if (cta < 256 || cta > 1024 || cta % 32) return AES_ERR_ARG;
+  if (tile < cta || tile > 65536 || tile % cta) return AES_ERR_ARG;
+  if (grid < 1) return AES_ERR_ARG;
+  const void* din = nullptr;
+  void* dout = nullptr;
+  aes_status st = device_view(b->in, &din);
+  if (st != AES_OK) return st;
+  const void* o = nullptr;
+  st = device_view(b->out, &o);
+  if (st != AES_OK) return st;
+  dout = const_cast<void*>(o);
+  BatchArgs a{};
+  a.n = b->n_msgs;
+  a.op = b->op;
+  a.in = static_cast<const uint8_t*>(din);
+  a.out = static_cast<uint8_t*>(dout);
+  a.in_off = b->in_off;
+  a.in_len = b->in_len;
+  a.out_off = b->out_off;
+  a.keys = b->keys;
+  a.key_bits = b->key_bits;
+  a.schedules = raw_keys ? nullptr : b->schedules;
+  a.sched_idx = raw_keys ? nullptr : b->sched_idx;
+  a.n_sched = raw_keys ? 0 : b->n_schedules;
+  a.tile_blocks = static_cast<uint32_t>(tile);
+  a.iv = b->iv;
+  a.out_len = b->out_len;
+  a.status = b->status;
+  batch_bind_workspace(&a, ws);
+  const cudaError_t e = launch_batch(a, cta, grid, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_failure(e);
+  return AES_OK;
+}
+
 }  // namespace
 }  // namespace aesgpu
 
@@ -264,6 +321,18 @@ aes_status aes_ecb_decrypt(const aes_key_schedule* ks, const void* d_in, void* d
 aes_status aes_ctr_xcrypt(const aes_key_schedule* ks, const uint8_t iv[16], const void* d_in,
                           void* d_out, size_t nbytes, void* stream) {
   return aes_ctr_xcrypt_ex(ks, iv, d_in, d_out, nbytes, stream, nullptr);
+}
+
+size_t aes_batch_workspace_size(uint32_t n_msgs) { return batch_workspace_bytes(n_msgs); }
+
+aes_status aes_batch_submit_ex(const aes_batch* b, void* d_workspace, size_t workspace_bytes,
+                               void* stream, const aes_batch_config* cfg) {
+  return batch_submit(b, d_workspace, workspace_bytes, stream, cfg);
+}
+
+aes_status aes_batch_submit(const aes_batch* b, void* d_workspace, size_t workspace_bytes,
+                            void* stream) {
+  return batch_submit(b, d_workspace, workspace_bytes, stream, nullptr);
 }
 
 int aes_last_cuda_error(void) { return g_last_cuda_error; }

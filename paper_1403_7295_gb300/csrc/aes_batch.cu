@@ -1,0 +1,522 @@
+// aes_batch.cu — batched varlen AES: many messages, each with its own key
+// and IV, in one persistent launch (the paper's chunk-per-thread scheme of
+// §IV.B with chunks = messages, mapped onto blocks of a GPU grid).
+//
+// Pipeline on the caller's stream:
+//   1. batch_count_scan  per message: validate, count 16-byte blocks
+//      (CTR ceil(len/16); ECB+PKCS#7 encrypt floor(len/16)+1; decrypt len/16),
+//      write status/out_len, exclusive-scan the counts inside chunks of 4096
+//      messages; reset the tile counter.
+//   2. batch_scan_chunks one CTA scans the chunk totals and writes the grand total.
+//   3. batch_scan_fix    adds each chunk's offset: blk_off[m] = first global block of m.
+//   4. batch_kernel      persistent CTAs claim tiles of `tile_blocks` blocks with an
+//      atomic counter, find the tile's messages by a 32-way warp search over
+//      blk_off, expand their keys on the device into shared memory (one thread
+//      per message, FIPS-197 §5.2; the equivalent inverse schedule for ECB
+//      decryption), then run the T-table rounds of aes_ttable.cuh with round
+//      keys read from shared memory (one 128-bit broadcast load per round).
+#include "aes_batch.h"
+#include "aes_ttable.cuh"
+
+namespace aesgpu {
+namespace {
+
+constexpr uint32_t kScanThreads = 1024;
+constexpr uint32_t kScanItems = 4;
+constexpr uint32_t kRkStride = 68;  // words per schedule slot: 16-B aligned, skews banks by 4
+
+template <int OPB>
+struct WindowSize;
+template <>
+struct WindowSize<kBatchCtr> {
+  static constexpr int value = 256;
+};
+template <>
+struct WindowSize<kBatchEcbEnc> {
+  static constexpr int value = 256;
+};
+template <>
+struct WindowSize<kBatchEcbDec> {
+  static constexpr int value = 96;
+};
+
+struct Slot {
+  uint64_t blk_start;  // global index of the message's first block
+  uint64_t blk_end;
+  uint64_t in_off, out_off, len;
+  uint32_t nr, msg;
+  uint32_t c1[4];
+  uint32_t rk0w3, ctr0;
+};
+
+template <int OPB>
+constexpr size_t batch_table_bytes() {
+  return OPB == kBatchEcbDec ? 192 * 1024 : 128 * 1024;
+}
+
+template <int OPB>
+constexpr size_t batch_smem_bytes() {
+  return batch_table_bytes<OPB>() + WindowSize<OPB>::value * (kRkStride * 4 + sizeof(Slot));
+}
+
+// ---------------------------------------------------------------- scan ----
+
+__device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m) {
+  const uint64_t len = a.in_len[m];
+  int32_t st = AES_OK;
+  if ((a.in_off[m] | a.out_off[m]) & 15u) st = AES_ERR_ALIGN;
+  if (a.keys != nullptr) {
+    const uint32_t bits = a.key_bits[m];
+    if (bits != 128 && bits != 192 && bits != 256) st = AES_ERR_KEYSIZE;
+  } else {
+    const uint32_t idx = a.sched_idx[m];
+    if (idx >= a.n_sched) {
+      st = AES_ERR_ARG;
+    } else {
+      const uint32_t bits = a.schedules[idx].key_bits, nr = a.schedules[idx].nr;
+      if (!((bits == 128 && nr == 10) || (bits == 192 && nr == 12) || (bits == 256 && nr == 14)))
+        st = AES_ERR_KEYSIZE;
+    }
+  }
+  uint64_t nb = 0, olen = 0;
+  if (a.op == kBatchCtr) {
+    nb = (len + 15) / 16;
+    olen = len;
+  } else if (a.op == kBatchEcbEnc) {
+    nb = len / 16 + 1;
+    olen = 16 * nb;
+  } else {
+    if (len == 0 || (len & 15u)) st = AES_ERR_LENGTH;
+    nb = len / 16;
+    olen = 0;  // set after the padding check
+  }
+  if (st != AES_OK) nb = olen = 0;
+  if (a.status) a.status[m] = st;
+  if (a.out_len) a.out_len[m] = olen;
+  return nb;
+}
+
+// Exclusive scan of one value per thread across the CTA; *total = CTA sum.
+__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* sh, uint64_t* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= static_cast<uint32_t>(o)) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < nwarps ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= static_cast<uint32_t>(o)) w += y;
+    }
+    sh[32 + lane] = w;  // inclusive warp prefixes
+  }
+  __syncthreads();
+  const uint64_t before = warp ? sh[32 + warp - 1] : 0;
+  *total = sh[32 + nwarps - 1];
+  __syncthreads();  // sh may be reused by the caller
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_count_scan(const BatchArgs a) {
+  __shared__ uint64_t sh[64];
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems +
+                        static_cast<uint64_t>(threadIdx.x) * kScanItems;
+  uint64_t cnt[kScanItems], sum = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < kScanItems; ++k) {
+    const uint64_t m = base + k;
+    cnt[k] = m < a.n ? count_blocks(a, static_cast<uint32_t>(m)) : 0;
+    sum += cnt[k];
+  }
+  uint64_t total;
+  uint64_t run = cta_exclusive_scan(sum, sh, &total);
+#pragma unroll
+  for (uint32_t k = 0; k < kScanItems; ++k) {
+    const uint64_t m = base + k;
+    if (m < a.n) a.blk_off[m] = run;
+    run += cnt[k];
+  }
+  if (threadIdx.x == 0) {
+    a.chunk_sum[blockIdx.x] = total;
+    if (gridDim.x == 1) a.blk_off[a.n] = total;
+    if (blockIdx.x == 0) *a.tile_counter = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_scan_chunks(const BatchArgs a) {
+  __shared__ uint64_t sh[64];
+  uint64_t carry = 0;
+  for (uint32_t c0 = 0; c0 < a.nchunks; c0 += kScanThreads) {
+    const uint32_t c = c0 + threadIdx.x;
+    const uint64_t v = c < a.nchunks ? a.chunk_sum[c] : 0;
+    uint64_t total;
+    const uint64_t ex = cta_exclusive_scan(v, sh, &total);
+    if (c < a.nchunks) a.chunk_sum[c] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) a.blk_off[a.n] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_scan_fix(const BatchArgs a) {
+  const uint64_t add = a.chunk_sum[blockIdx.x];
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems;
+  for (uint32_t k = threadIdx.x; k < kScanThreads * kScanItems; k += blockDim.x) {
+    const uint64_t m = base + k;
+    if (m < a.n) a.blk_off[m] += add;
+  }
+}
+
+// ------------------------------------------------------------ persistent ----
+
+// Largest m in [0, n) with blk_off[m] <= g (blk_off non-decreasing, blk_off[0] = 0),
+// by a 32-way search: each step narrows the range 32-fold.  Whole warp calls.
+__device__ __forceinline__ uint32_t warp_find(const uint64_t* blk_off, uint32_t n, uint64_t g) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint64_t idx = static_cast<uint64_t>(lo) + static_cast<uint64_t>(lane) * step;
+    const bool ok = lane == 0 || (idx < hi && blk_off[idx] <= g);
+    const uint32_t mask = __ballot_sync(0xffffffffu, ok);
+    const uint32_t last = 31 - __clz(mask);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
+// S(x) for each byte of w.  `sb` points at a replicated table whose byte 0 is S(x).
+__device__ __forceinline__ uint32_t sub_word(const Tabs& T, const char* sb, uint32_t off,
+                                             uint32_t w) {
+  const uint32_t a = T.ld(sb, w, off, 0x5504), b = T.ld(sb, w, off, 0x5514);
+  const uint32_t c = T.ld(sb, w, off, 0x5524), d = T.ld(sb, w, off, 0x5534);
+  return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
+}
+
+__device__ __forceinline__ uint32_t load_le32(const uint8_t* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// FIPS-197 §5.2 into rk[0 .. 4(nr+1)).  key: 4-byte aligned, nk words.
+__device__ void expand_key(const Tabs& T, const char* sb, uint32_t sb_off, const uint8_t* key,
+                           uint32_t nk, uint32_t nr, uint32_t* rk) {
+  for (uint32_t i = 0; i < nk; ++i) rk[i] = load_le32(key + 4 * i);
+  uint32_t rcon = 1;
+  const uint32_t nwords = 4 * (nr + 1);
+  for (uint32_t i = nk; i < nwords; ++i) {
+    uint32_t t = rk[i - 1];
+    if (i % nk == 0) {
+      t = sub_word(T, sb, sb_off, __funnelshift_r(t, t, 8)) ^ rcon;  // RotWord, SubWord, Rcon
+      rcon = ((rcon << 1) ^ ((rcon & 0x80u) ? 0x1Bu : 0u)) & 0xFFu;
+    } else if (nk == 8 && i % nk == 4) {
+      t = sub_word(T, sb, sb_off, t);
+    }
+    rk[i] = rk[i - nk] ^ t;
+  }
+}
+
+// Turn an encryption schedule into the equivalent inverse cipher's (FIPS-197
+// §5.3.5), in place.  InvMixColumns(w) = sum_i TDi[S(byte i of w)], since each
+// td word applies the inverse S-box first.
+__device__ void to_decrypt_schedule(const Tabs& T, const char* sb, uint32_t sb_off, uint32_t nr,
+                                    uint32_t* rk) {
+  auto inv_mix = [&](uint32_t w) {
+    const uint32_t s = sub_word(T, sb, sb_off, w);
+    return T.t0(s) ^ T.t1(s) ^ T.t2(s) ^ T.t3(s);
+  };
+  for (uint32_t r = 0; r <= nr / 2; ++r) {
+    const uint32_t q = nr - r;
+    for (uint32_t c = 0; c < 4; ++c) {
+      const uint32_t a = rk[4 * r + c], b = rk[4 * q + c];
+      const uint32_t na = (q == 0 || q == nr) ? b : inv_mix(b);  // new round r from old round q
+      const uint32_t nb = (r == 0 || r == nr) ? a : inv_mix(a);  // new round q from old round r
+      rk[4 * r + c] = na;
+      if (q != r) rk[4 * q + c] = nb;
+    }
+  }
+}
+
+__device__ __forceinline__ uint4 lds128(const uint32_t* p) {
+  return *reinterpret_cast<const uint4*>(p);
+}
+
+template <int NR>
+__device__ __forceinline__ State enc_rounds_smem(const Tabs& T, State s, const uint32_t* rk,
+                                                 int first) {
+#pragma unroll
+  for (int r = 1; r < NR; ++r) {
+    if (r < first) continue;
+    const uint4 k = lds128(rk + 4 * r);
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+    enc_round(T, s, kk);
+  }
+  const uint4 k = lds128(rk + 4 * NR);
+  const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+  enc_final(T, s, kk);
+  return s;
+}
+
+template <int NR>
+__device__ __forceinline__ State dec_rounds_smem(const Tabs& T, State s, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 1; r < NR; ++r) {
+    const uint4 k = lds128(rk + 4 * r);
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+    dec_round(T, s, kk);
+  }
+  const uint4 k = lds128(rk + 4 * NR);
+  const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+  dec_final(T, s, kk);
+  return s;
+}
+
+__device__ __forceinline__ State enc_any(const Tabs& T, State s, const uint32_t* rk, uint32_t nr,
+                                         int first) {
+  switch (nr) {
+    case 10: return enc_rounds_smem<10>(T, s, rk, first);
+    case 12: return enc_rounds_smem<12>(T, s, rk, first);
+    default: return enc_rounds_smem<14>(T, s, rk, first);
+  }
+}
+
+__device__ __forceinline__ State dec_any(const Tabs& T, State s, const uint32_t* rk, uint32_t nr) {
+  switch (nr) {
+    case 10: return dec_rounds_smem<10>(T, s, rk);
+    case 12: return dec_rounds_smem<12>(T, s, rk);
+    default: return dec_rounds_smem<14>(T, s, rk);
+  }
+}
+
+__device__ __forceinline__ uint32_t state_byte(const State& s, uint32_t k) {
+  const uint32_t w = k < 4 ? s.s0 : k < 8 ? s.s1 : k < 12 ? s.s2 : s.s3;
+  return (w >> (8 * (k & 3))) & 0xFFu;
+}
+
+// Fill slot `t` of the window with message m: offsets, key schedule, CTR constants.
+template <int OPB>
+__device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uint32_t sb_off,
+                          uint32_t m, Slot& sl, uint32_t* rk) {
+  sl.blk_start = a.blk_off[m];
+  sl.blk_end = a.blk_off[m + 1];
+  sl.msg = m;
+  sl.nr = 10;
+  if (sl.blk_end == sl.blk_start) return;  // empty or rejected: never selected
+  sl.in_off = a.in_off[m];
+  sl.out_off = a.out_off[m];
+  sl.len = a.in_len[m];
+  if (a.keys != nullptr) {
+    const uint32_t bits = a.key_bits[m];
+    const uint32_t nk = bits / 32, nr = nk + 6;
+    sl.nr = nr;
+    expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, nr, rk);
+    if (OPB == kBatchEcbDec) to_decrypt_schedule(T, sb, sb_off, nr, rk);
+  } else {
+    const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
+    const uint32_t nr = ks.nr;
+    sl.nr = nr;
+    const uint32_t* src = OPB == kBatchEcbDec ? ks.rk_dec : ks.rk_enc;
+    for (uint32_t i = 0; i < 4 * (nr + 1); ++i) rk[i] = src[i];
+  }
+  if (OPB == kBatchCtr) {
+    const uint4 ivw = *reinterpret_cast<const uint4*>(a.iv + 16ull * m);
+    const uint32_t iv_w[4] = {ivw.x, ivw.y, ivw.z, ivw.w};
+    sl.ctr0 = __byte_perm(ivw.w, 0, 0x0123);
+    uint32_t s[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = iv_w[c] ^ rk[c];
+    s[3] = 0;  // the counter column: looked up per block
+    sl.rk0w3 = rk[3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t acc = rk[4 + j];
+      // row i of round-1 column j comes from column j+i; column 3 (the counter) stays on the device
+      if (((j + 0) & 3) != 3) acc ^= T.t0(s[(j + 0) & 3]);
+      if (((j + 1) & 3) != 3) acc ^= T.t1(s[(j + 1) & 3]);
+      if (((j + 2) & 3) != 3) acc ^= T.t2(s[(j + 2) & 3]);
+      if (((j + 3) & 3) != 3) acc ^= T.t3(s[(j + 3) & 3]);
+      sl.c1[j] = acc;
+    }
+  }
+}
+
+template <int OPB>
+__device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T, const Slot& sl,
+                                              const uint32_t* rk, uint64_t g) {
+  const uint64_t j = g - sl.blk_start;
+  const uint64_t off = 16 * j;
+  const uint8_t* src = a.in + sl.in_off + off;
+  uint8_t* dst = a.out + sl.out_off + off;
+  const bool full = off + 16 <= sl.len;
+  if (OPB == kBatchCtr) {
+    const uint32_t ctr = sl.ctr0 + static_cast<uint32_t>(j);
+    const uint32_t x = __byte_perm(ctr, 0, 0x0123) ^ sl.rk0w3;
+    State s{sl.c1[0] ^ T.t3(x), sl.c1[1] ^ T.t2(x), sl.c1[2] ^ T.t1(x), sl.c1[3] ^ T.t0(x)};
+    s = enc_any(T, s, rk, sl.nr, 2);
+    if (full) {
+      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src));
+      __stcs(reinterpret_cast<uint4*>(dst), make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3));
+    } else {
+      const uint32_t rem = static_cast<uint32_t>(sl.len - off);
+      for (uint32_t b = 0; b < rem; ++b) dst[b] = src[b] ^ static_cast<uint8_t>(state_byte(s, b));
+    }
+  } else if (OPB == kBatchEcbEnc) {
+    uint4 v;
+    if (full) {
+      v = __ldcs(reinterpret_cast<const uint4*>(src));
+    } else {  // last block: rem message bytes then PKCS#7 pad bytes (1..16 of value 16 - rem)
+      const uint32_t rem = static_cast<uint32_t>(sl.len - off);
+      const uint32_t pad = 16 - rem;
+      uint32_t w[4];
+      for (int q = 0; q < 4; ++q) {
+        uint32_t acc = 0;
+        for (int b = 0; b < 4; ++b) {
+          const uint32_t k = 4 * q + b;
+          const uint32_t byte = k < rem ? src[k] : pad;
+          acc |= byte << (8 * b);
+        }
+        w[q] = acc;
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    const uint4 k0 = lds128(rk);
+    State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+    s = enc_any(T, s, rk, sl.nr, 1);
+    __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
+  } else {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src));
+    const uint4 k0 = lds128(rk);
+    State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+    s = dec_any(T, s, rk, sl.nr);
+    __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
+    if (g + 1 == sl.blk_end) {  // last block: check PKCS#7
+      const uint32_t p = state_byte(s, 15);
+      bool ok = p >= 1 && p <= 16;
+      for (uint32_t k = 16 - (ok ? p : 0); k < 16; ++k) ok = ok && state_byte(s, k) == p;
+      if (a.status) a.status[sl.msg] = ok ? AES_OK : AES_ERR_PADDING;
+      if (a.out_len) a.out_len[sl.msg] = ok ? sl.len - p : 0;
+    }
+  }
+}
+
+template <int OPB>
+__global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
+  constexpr int kWin = WindowSize<OPB>::value;
+  constexpr bool kDec = OPB == kBatchEcbDec;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ unsigned long long s_tile;
+  __shared__ uint32_t s_mlo, s_mhi;
+
+  fill_tables<kDec>(smem);
+  if (kDec) {  // forward S-box (all four bytes) beside the inverse one, for key expansion
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int x = warp; x < 256; x += nwarps)
+      smem[kRegionC / 4 + x * 64 + 32 + lane] = kDevTables.sbox[x] * 0x01010101u;
+  }
+  uint32_t* rk_all = smem + batch_table_bytes<OPB>() / 4;
+  Slot* slots = reinterpret_cast<Slot*>(rk_all + kWin * kRkStride);
+  __syncthreads();
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const char* base = reinterpret_cast<const char*>(smem);
+  const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
+  // S-box source for key expansion: byte 0 of te2 (encryption tables) or the
+  // forward S-box words in the upper half of region C (decryption tables).
+  const char* sb = kDec ? T.c : T.b;
+  const uint32_t sb_off = kDec ? T.hi : T.lo;
+
+  const uint64_t total = a.blk_off[a.n];
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1ull);
+    __syncthreads();
+    const uint64_t t0 = s_tile * a.tile_blocks;
+    if (t0 >= total) break;
+    const uint64_t t1 = min(t0 + a.tile_blocks, total);
+    if (warp == 0) {
+      const uint32_t m = warp_find(a.blk_off, a.n, t0);
+      if (lane == 0) s_mlo = m;
+    } else if (warp == 1) {
+      const uint32_t m = warp_find(a.blk_off, a.n, t1 - 1);
+      if (lane == 0) s_mhi = m;
+    }
+    __syncthreads();
+    const uint32_t m_lo = s_mlo, m_hi = s_mhi;
+    for (uint32_t w0 = m_lo; w0 <= m_hi; w0 += kWin) {
+      const uint32_t wn = min(static_cast<uint32_t>(kWin), m_hi - w0 + 1);
+      if (tid < wn) load_slot<OPB>(a, T, sb, sb_off, w0 + tid, slots[tid], rk_all + tid * kRkStride);
+      __syncthreads();
+      const uint64_t g0 = max(t0, slots[0].blk_start);
+      const uint64_t g1 = min(t1, slots[wn - 1].blk_end);
+      for (uint64_t g = g0 + tid; g < g1; g += blockDim.x) {
+        // slot of block g: last slot whose first block is <= g
+        uint32_t lo = 0, hi = wn;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (slots[mid].blk_start <= g) lo = mid;
+          else hi = mid;
+        }
+        process_block<OPB>(a, T, slots[lo], rk_all + lo * kRkStride, g);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int OPB>
+cudaError_t launch_persistent(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
+  constexpr size_t smem = batch_smem_bytes<OPB>();
+  static_assert(smem + 64 <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
+  auto kern = batch_kernel<OPB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, cta, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t batch_workspace_bytes(uint32_t n) {
+  const size_t nchunks = (static_cast<size_t>(n) + kScanThreads * kScanItems - 1) /
+                         (kScanThreads * kScanItems);
+  auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  return up(8 * (static_cast<size_t>(n) + 1)) + up(8 * (nchunks > 0 ? nchunks : 1)) + 256;
+}
+
+void batch_bind_workspace(BatchArgs* a, void* ws) {
+  auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  const size_t nchunks = (static_cast<size_t>(a->n) + kScanThreads * kScanItems - 1) /
+                         (kScanThreads * kScanItems);
+  char* p = static_cast<char*>(ws);
+  a->blk_off = reinterpret_cast<uint64_t*>(p);
+  p += up(8 * (static_cast<size_t>(a->n) + 1));
+  a->chunk_sum = reinterpret_cast<uint64_t*>(p);
+  p += up(8 * (nchunks > 0 ? nchunks : 1));
+  a->tile_counter = reinterpret_cast<unsigned long long*>(p);
+  a->nchunks = static_cast<uint32_t>(nchunks);
+}
+
+cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
+  batch_count_scan<<<a.nchunks, kScanThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.nchunks > 1) {
+    batch_scan_chunks<<<1, kScanThreads, 0, s>>>(a);
+    batch_scan_fix<<<a.nchunks, kScanThreads, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  switch (a.op) {
+    case kBatchCtr: return launch_persistent<kBatchCtr>(a, cta, grid, s);
+    case kBatchEcbEnc: return launch_persistent<kBatchEcbEnc>(a, cta, grid, s);
+    case kBatchEcbDec: return launch_persistent<kBatchEcbDec>(a, cta, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace aesgpu

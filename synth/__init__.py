@@ -31,7 +31,7 @@ STREAM_MISC = 4
 
 
 def _base(seed: int, stream: int) -> int:
-    return ((seed << 40) + (stream << 32)) & MASK64
+    return ((int(seed) << 40) + (int(stream) << 32)) & MASK64
 
 
 def words_np(seed: int, stream: int, count: int, start: int = 0) -> np.ndarray:

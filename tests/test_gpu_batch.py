@@ -1,0 +1,301 @@
+"""GPU parity of the batched path: every message equals the oracle run on that
+message alone, bit for bit.
+
+Covers CTR, ECB+PKCS#7 encrypt and decrypt; mixed key sizes; raw keys
+expanded on the device and pre-expanded schedule tables; empty, 1-byte,
+block-sized and ragged messages; batches large enough for the chunked scan
+(> 4096 messages) and for many key windows per tile (thousands of one-block
+messages per tile); per-message failures (bad key size, misaligned offset,
+bad ECB length, bad padding) that leave the rest of the batch intact;
+CUDA-graph replay; and the full-size batched workloads (16,384 log-uniform
+messages, 64 B .. 4 MiB; 1,000,000 packet-sized messages) on sampled
+messages.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from synth import workloads as W
+from tests.gpu_util import host_threads, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+@pytest.fixture(scope="module")
+def B(torch):
+    from paper_1403_7295_gb300 import batch
+
+    return batch
+
+
+def build(B, torch, op, lengths, key_bits, keys, ivs, seed, **kw):
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(seed, synth.STREAM_DATA, max(total, 16), device="cuda")
+    return B.Batch(op, data, in_off, lengths, keys=keys, key_bits=key_bits, ivs=ivs, **kw)
+
+
+def oracle_check(B, oracle, batch, key_bits, keys, ivs, idx=None, check_status=True):
+    data = batch.data.cpu().numpy()
+    out = batch.out.cpu().numpy()
+    out_len = batch.out_len.cpu().numpy()
+    status = batch.status.cpu().numpy()
+    in_off = batch.in_off.cpu().numpy()
+    ms = range(batch.n) if idx is None else idx
+    for m in ms:
+        ln = int(batch.lengths_np[m])
+        bits = int(key_bits[m])
+        key = keys[m][: bits // 8]
+        io = int(in_off[m])
+        msg = data[io: io + ln]
+        oo = int(batch.out_off_np[m])
+        if batch.op == B.BATCH_CTR:
+            want = oracle.ctr_xcrypt(key, bits, ivs[m], msg)
+            assert status[m] == 0 and out_len[m] == ln, m
+            assert np.array_equal(out[oo: oo + ln], want), m
+        elif batch.op == B.BATCH_ECB_PKCS7_ENCRYPT:
+            want = oracle.ecb_pkcs7_encrypt(key, bits, msg)
+            assert status[m] == 0 and out_len[m] == want.size, m
+            assert np.array_equal(out[oo: oo + want.size], want), m
+        else:
+            rc, pt = oracle.ecb_pkcs7_decrypt(key, bits, msg)
+            if rc == 0:
+                assert status[m] == 0 and out_len[m] == pt.size, m
+                assert np.array_equal(out[oo: oo + pt.size], pt), m
+            else:
+                assert status[m] == 6 and out_len[m] == 0, m
+
+
+def mixed_lengths(seed, n):
+    special = np.array([0, 1, 15, 16, 17, 31, 32, 33, 255, 256, 4095, 4096, 4097], np.uint64)
+    rest = W.uniform_lengths(seed, n - special.size, 0, 5000)
+    return np.concatenate([special, rest])
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_batch_small_messages_all_key_sizes(torch, B, oracle, op):
+    n = 400
+    lengths = mixed_lengths(1 + op, n)
+    kb = W.key_sizes(1, n)
+    keys = W.message_keys(1, n)
+    ivs = W.message_ivs(1, n, counter0=0xFFFFFFF0)  # every message with > 16 blocks wraps
+    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=11).submit()
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, b, kb, keys, ivs)
+
+
+def test_batch_decrypt_round_trip_and_bad_padding(torch, B, oracle):
+    n = 300
+    lengths = mixed_lengths(5, n)
+    kb = W.key_sizes(5, n)
+    keys = W.message_keys(5, n)
+    enc = build(B, torch, B.BATCH_ECB_PKCS7_ENCRYPT, lengths, kb, keys, None, seed=12).submit()
+    torch.cuda.synchronize()
+    ct_len = enc.out_len.cpu().numpy().astype(np.uint64)
+    # corrupt the last byte of a few ciphertexts: their padding check must fail (almost surely)
+    bad = [3, 50, 299]
+    out = enc.out.clone()
+    for m in bad:
+        pos = int(enc.out_off_np[m] + ct_len[m] - 1)
+        out[pos] ^= 0x5A
+    dec = B.Batch(B.BATCH_ECB_PKCS7_DECRYPT, out, enc.out_off_np, ct_len, keys=keys, key_bits=kb).submit()
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, dec, kb, keys, None)
+    st = dec.status.cpu().numpy()
+    ol = dec.out_len.cpu().numpy()
+    src = enc.data.cpu().numpy()
+    res = dec.out.cpu().numpy()
+    in_off = enc.in_off.cpu().numpy()
+    for m in range(n):
+        if m in bad:
+            continue
+        assert st[m] == 0 and ol[m] == lengths[m]
+        o, i, ln = int(dec.out_off_np[m]), int(in_off[m]), int(lengths[m])
+        assert np.array_equal(res[o: o + ln], src[i: i + ln])
+
+
+def test_batch_schedule_table_matches_raw_keys(torch, B, oracle):
+    from paper_1403_7295_gb300 import aes as A
+
+    n = 257
+    lengths = mixed_lengths(7, n)
+    kb = W.key_sizes(7, n)
+    keys = W.message_keys(7, n)
+    ivs = W.message_ivs(7, n)
+    n_tenants = 37
+    tid = (np.arange(n) * 7) % n_tenants
+    tkeys = W.message_keys(70, n_tenants)
+    tbits = W.key_sizes(70, n_tenants)
+    table = b"".join(bytes(A.aes_expand_key(tkeys[t][: tbits[t] // 8], int(tbits[t]))) for t in range(n_tenants))
+    sched = torch.frombuffer(bytearray(table), dtype=torch.uint8).cuda()
+    for op in (0, 1):
+        b = build(B, torch, op, lengths, None, None, ivs if op == 0 else None, seed=13,
+                  schedules=sched, n_schedules=n_tenants, sched_idx=tid).submit()
+        torch.cuda.synchronize()
+        oracle_check(B, oracle, b, tbits[tid], tkeys[tid], ivs)
+    enc = b  # op 1 output: decrypt it through the schedule table too
+    ct_len = enc.out_len.cpu().numpy().astype(np.uint64)
+    dec = B.Batch(B.BATCH_ECB_PKCS7_DECRYPT, enc.out, enc.out_off_np, ct_len, schedules=sched,
+                  n_schedules=n_tenants, sched_idx=tid).submit()
+    torch.cuda.synchronize()
+    assert np.array_equal(dec.out_len.cpu().numpy(), lengths.astype(np.int64))
+
+
+def test_batch_many_tiny_messages_multi_window(torch, B, oracle):
+    """20,000 one-block messages: > 4096 (chunked scan) and thousands per tile."""
+    n = 20000
+    lengths = W.uniform_lengths(9, n, 1, 16)
+    kb = W.key_sizes(9, n)
+    keys = W.message_keys(9, n)
+    ivs = W.message_ivs(9, n)
+    b = build(B, torch, 0, lengths, kb, keys, ivs, seed=14)
+    for cfg in (None, B.AesBatchConfig(256, 256, 0, 0), B.AesBatchConfig(1024, 32768, 3, 0)):
+        b.out.fill_(0)
+        b.submit(config=cfg)
+        torch.cuda.synchronize()
+        oracle_check(B, oracle, b, kb, keys, ivs)
+
+
+def test_batch_per_message_errors(torch, B, oracle):
+    n = 64
+    lengths = mixed_lengths(10, n)
+    kb = W.key_sizes(10, n).copy()
+    keys = W.message_keys(10, n)
+    ivs = W.message_ivs(10, n)
+    in_off, total = B.pack_offsets(lengths + np.uint64(16))
+    in_off = in_off.copy()
+    kb[5] = 100          # bad key size
+    in_off[9] += 8       # misaligned message
+    data = synth.bytes_torch(15, synth.STREAM_DATA, total + 32, device="cuda")
+    b = B.Batch(0, data, in_off, lengths, keys=keys, key_bits=kb, ivs=ivs).submit()
+    torch.cuda.synchronize()
+    st = b.status.cpu().numpy()
+    assert st[5] == 2 and st[9] == 4
+    ok = [m for m in range(n) if m not in (5, 9)]
+    oracle_check(B, oracle, b, kb, keys, ivs, idx=ok)
+    # ECB decrypt with a length that is not a positive multiple of 16
+    lens = np.array([32, 17, 0, 48], np.uint64)
+    b2 = build(B, torch, 2, lens, np.full(4, 128, np.uint32), W.message_keys(11, 4), None, seed=16).submit()
+    torch.cuda.synchronize()
+    st = b2.status.cpu().numpy()
+    assert st[1] == 3 and st[2] == 3
+
+
+def test_batch_host_validation(torch, B):
+    from paper_1403_7295_gb300 import aes as A
+
+    lengths = np.array([16, 32], np.uint64)
+    b = build(B, torch, 0, lengths, np.array([128, 128], np.uint32), W.message_keys(1, 2),
+              W.message_ivs(1, 2), seed=17)
+    L = B._declare()
+    ws = b.workspace
+    assert L.aes_batch_submit(ctypes.byref(b.desc), ws.data_ptr(), 8, None) == 7  # short workspace
+    d = B.AesBatch.from_buffer_copy(b.desc)
+    d.op = 9
+    assert L.aes_batch_submit(ctypes.byref(d), ws.data_ptr(), ws.numel(), None) == 1
+    d = B.AesBatch.from_buffer_copy(b.desc)
+    d.iv = None
+    assert L.aes_batch_submit(ctypes.byref(d), ws.data_ptr(), ws.numel(), None) == 1
+    d = B.AesBatch.from_buffer_copy(b.desc)
+    d.in_ = b.data.data_ptr() + 4
+    assert L.aes_batch_submit(ctypes.byref(d), ws.data_ptr(), ws.numel(), None) == 4
+    cfg = B.AesBatchConfig(1024, 1000, 0, 0)  # tile not a multiple of the CTA
+    with pytest.raises(A.AesError):
+        b.submit(config=cfg)
+    d = B.AesBatch.from_buffer_copy(b.desc)
+    d.n_msgs = 0
+    assert L.aes_batch_submit(ctypes.byref(d), None, 0, None) == 0
+
+
+def test_batch_graph_replay_is_deterministic(torch, B, oracle):
+    n = 1000
+    lengths = W.log_uniform_lengths(21, n, 16, 1 << 16)
+    kb = W.key_sizes(21, n)
+    keys = W.message_keys(21, n)
+    ivs = W.message_ivs(21, n)
+    b = build(B, torch, 0, lengths, kb, keys, ivs, seed=18)
+    b.out.fill_(0)  # slot padding is never written: start from a known arena
+    b.submit()
+    torch.cuda.synchronize()
+    first = b.out.clone()
+    b.capture()
+    for _ in range(2):
+        b.out.fill_(0)
+        b.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(b.out, first)
+    oracle_check(B, oracle, b, kb, keys, ivs, idx=range(0, n, 7))
+
+
+def sampled_check_large(B, oracle, b, key_bits, keys, ivs, ms, max_full=1 << 20):
+    """Messages up to max_full bytes compared whole; larger ones on 256 sampled blocks."""
+    import torch
+
+    for m in ms:
+        ln = int(b.lengths_np[m])
+        bits = int(key_bits[m])
+        key = keys[m][: bits // 8]
+        io = int(b.in_off[m].item())
+        oo = int(b.out_off_np[m])
+        if ln <= max_full:
+            msg = b.data[io: io + ln].cpu().numpy()
+            got = b.out[oo: oo + ln].cpu().numpy()
+            assert np.array_equal(got, oracle.ctr_xcrypt(key, bits, ivs[m], msg)), m
+        else:
+            nb = ln // 16
+            idx = np.unique((synth.uniform01(m, synth.STREAM_MISC, 256) * nb).astype(np.uint64))
+            t = torch.from_numpy(idx.astype(np.int64)).cuda()
+            blocks = b.data[io: io + 16 * nb].view(-1, 16)[t].cpu().numpy()
+            got = b.out[oo: oo + 16 * nb].view(-1, 16)[t].cpu().numpy()
+            want = oracle.ctr_xcrypt_blocks(key, bits, ivs[m], idx, blocks)
+            assert np.array_equal(got.reshape(-1), want), m
+
+
+def test_full_size_batched_varlen_16384(torch, B, oracle):
+    """16,384 messages, log-uniform 64 B .. 4 MiB, mixed key sizes (≈6 GB):
+    CTR sampled against the oracle; ECB+PKCS#7 encrypt then decrypt on the
+    device gives back every message."""
+    wl = W.batched_varlen(3, 16384)
+    lengths, kb, keys, ivs = wl["lengths"], wl["key_bits"], wl["keys"], wl["ivs"]
+    b = build(B, torch, 0, lengths, kb, keys, ivs, seed=19)
+    b.capture(B.autotune(b))
+    b.replay()
+    torch.cuda.synchronize()
+    assert int((b.status != 0).sum()) == 0
+    pick = np.unique((synth.uniform01(19, synth.STREAM_MISC, 48) * b.n).astype(np.int64))
+    biggest = int(np.argmax(lengths))
+    sampled_check_large(B, oracle, b, kb, keys, ivs, list(pick) + [biggest, 0, b.n - 1])
+    del b
+    torch.cuda.empty_cache()
+    enc = build(B, torch, 1, lengths, kb, keys, None, seed=20).submit()
+    torch.cuda.synchronize()
+    ct_len = enc.out_len.cpu().numpy().astype(np.uint64)
+    oracle_check(B, oracle, enc, kb, keys, None, idx=[m for m in range(0, 16384, 512) if lengths[m] < (1 << 18)])
+    dec = B.Batch(2, enc.out, enc.out_off_np, ct_len, keys=keys, key_bits=kb).submit()
+    torch.cuda.synchronize()
+    assert int((dec.status != 0).sum()) == 0
+    assert np.array_equal(dec.out_len.cpu().numpy(), lengths.astype(np.int64))
+    # plaintext back, compared on the device message by message (offsets differ only by padding)
+    src_off = enc.in_off.cpu().numpy()
+    for m in range(0, 16384, 97):
+        ln, o, i = int(lengths[m]), int(dec.out_off_np[m]), int(src_off[m])
+        assert torch.equal(dec.out[o: o + ln], enc.data[i: i + ln]), m
+
+
+def test_full_size_small_messages_1M(torch, B, oracle):
+    """1,000,000 messages of 16..1500 bytes, AES-128 CTR, keys expanded on the device."""
+    wl = W.small_messages(4, 1_000_000)
+    lengths, kb, keys, ivs = wl["lengths"], wl["key_bits"], wl["keys"], wl["ivs"]
+    b = build(B, torch, 0, lengths, kb, keys, ivs, seed=21)
+    b.capture(B.autotune(b))
+    b.replay()
+    torch.cuda.synchronize()
+    assert int((b.status != 0).sum()) == 0
+    pick = np.unique((synth.uniform01(21, synth.STREAM_MISC, 2000) * b.n).astype(np.int64))
+    oracle_check(B, oracle, b, kb, keys, ivs, idx=list(pick) + [0, b.n - 1])
