@@ -189,6 +189,32 @@ aes_status aes_batch_submit(const aes_batch *b, void *d_workspace, size_t worksp
 aes_status aes_batch_submit_ex(const aes_batch *b, void *d_workspace, size_t workspace_bytes,
                                void *stream, const aes_batch_config *cfg);
 
+/* aes_batch_submit without a workspace argument, for callers that cannot
+ * allocate device memory at all: code that runs where cudaMalloc is not
+ * allowed or not wanted (inside a host callback, on a latency-critical path
+ * where cudaMalloc's implicit device synchronisation would stall other
+ * streams, or inside a framework that owns every device allocation).  The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ * The workspace is one file-scope device array of the library, sized for
+ * AES_BATCH_NOALLOC_MAX_MSGS messages (about 513 KiB); every GPU that loads
+ * libaesgpu.so holds it until the process exits.  The call allocates nothing
+ * and calls no allocating routine; inputs and outputs are the caller's as in
+ * aes_batch_submit, with the same rules and per-message status.
+ *  - n_msgs above AES_BATCH_NOALLOC_MAX_MSGS returns AES_ERR_NOMEM and
+ *    enqueues nothing.
+ *  - The first call on a device looks up the array's device address there
+ *    (cudaGetSymbolAddress, which may load the library's GPU code): make that
+ *    first call before any stream capture on the device.
+ *  - All calls on a device share the one array, and it keeps the last call's
+ *    contents; the pipeline rewrites every part it reads (the first kernel
+ *    resets the tile counter and rewrites the offsets) before use.  Two calls
+ *    whose work overlaps on the GPU (different streams without ordering, or
+ *    host threads racing) corrupt each other's results: order them on one
+ *    stream or synchronise between them. */
+#define AES_BATCH_NOALLOC_MAX_MSGS 65536u
+aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
+
 /* The CUDA error code behind the calling thread's last AES_ERR_CUDA (0 if none). */
 int aes_last_cuda_error(void);
 

@@ -250,6 +250,10 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
 }
 
 }  // namespace
+
+// Records a CUDA failure for aes_last_cuda_error() from other translation units.
+aes_status record_cuda_failure(cudaError_t e) { return cuda_failure(e); }
+
 }  // namespace aesgpu
 
 using namespace aesgpu;

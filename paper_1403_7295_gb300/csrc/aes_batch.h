@@ -40,4 +40,7 @@ size_t batch_workspace_bytes(uint32_t n);
 void batch_bind_workspace(BatchArgs* a, void* ws);
 cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s);
 
+// Sets the calling thread's aes_last_cuda_error() and returns AES_ERR_CUDA.
+aes_status record_cuda_failure(cudaError_t e);
+
 }  // namespace aesgpu

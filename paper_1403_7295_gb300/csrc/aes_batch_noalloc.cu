@@ -1,0 +1,63 @@
+// aes_batch_noalloc.cu — aes_batch_submit for callers that cannot allocate:
+// the batch pipeline's workspace (per-message block offsets, chunk totals,
+// tile counter) lives in one file-scope device array instead of a caller
+// buffer.  The work itself is the ordinary aes_batch_submit path.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "aes_batch.h"
+#include "aesgpu.h"
+
+namespace {
+
+// Layout of the batch workspace for n messages: offsets (n + 1 words),
+// chunk totals (one word per 4096 messages), tile counter, each rounded up
+// to 256 bytes.
+constexpr size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+constexpr size_t workspace_for(size_t n) {
+  return round256(8 * (n + 1)) + round256(8 * ((n + 4095) / 4096)) + 256;
+}
+constexpr size_t kScratchBytes = workspace_for(AES_BATCH_NOALLOC_MAX_MSGS);  // 525,056 bytes
+
+// Held by every device that loads the library, for the life of the process.
+static __device__ __align__(256) unsigned char g_batch_scratch[kScratchBytes];
+
+// Device address of g_batch_scratch per device ordinal, looked up once with
+// that device current.  The host-side symbol is only a handle: its own
+// address is not usable on the device.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+aes_status scratch_for_current_device(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
+  if (dev < 0 || dev >= kMaxDevices) return AES_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    if (aesgpu::batch_workspace_bytes(AES_BATCH_NOALLOC_MAX_MSGS) > kScratchBytes)
+      return AES_ERR_NOMEM;  // layout drifted from the sizing above
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_batch_scratch);
+    if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return AES_OK;
+}
+
+}  // namespace
+
+extern "C" aes_status aes_batch_submit_noalloc(const aes_batch* b, void* stream) {
+  if (b == nullptr) return AES_ERR_ARG;
+  if (b->n_msgs > AES_BATCH_NOALLOC_MAX_MSGS) return AES_ERR_NOMEM;
+  if (b->n_msgs == 0) return AES_OK;
+  void* ws = nullptr;
+  const aes_status s = scratch_for_current_device(&ws);
+  if (s != AES_OK) return s;
+  // No counter needs clearing here: the pipeline's first kernel resets the
+  // tile counter and rewrites every offset the later kernels read.
+  return aes_batch_submit_ex(b, ws, kScratchBytes, stream, nullptr);
+}
