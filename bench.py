@@ -59,6 +59,11 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-probes", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-message workloads")
+    p.add_argument("--only", choices=["all", "batched"], default="all",
+                   help="'batched': time only the batched varlen workload (for profiling)")
+    p.add_argument("--batch-msgs", type=int, default=16384, help="messages in the batched varlen workload")
+    p.add_argument("--serve-seconds", type=float, default=10.0,
+                   help="duration of the serving leg (Poisson 50k req/s); 0 skips it")
     return p.parse_args()
 
 
@@ -206,6 +211,9 @@ def time_device(torch, fn, steps, warmup, barrier=None):
 def gpu_arm(args):
     import torch
 
+    if args.only == "batched":
+        return batched_only(args)
+
     from paper_1403_7295_gb300 import aes as A
     from paper_1403_7295_gb300 import build as B
 
@@ -310,6 +318,10 @@ def gpu_arm(args):
             torch.cuda.empty_cache()
             x = y = None
             result["batched"] = batched_arm(torch, A, value if world == 1 else None)
+        if args.serve_seconds > 0:
+            x = y = None
+            torch.cuda.empty_cache()
+            result["serving"] = serving_arm(torch, args.serve_seconds)
         del x, y
         torch.cuda.empty_cache()
         if not args.no_cpu:
@@ -360,6 +372,30 @@ def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):
 def time_graph(torch, b, steps):
     """CUDA-event time (ms) of `steps` replays of a captured batch graph."""
     return time_device(torch, b.replay, steps, 3)
+
+
+def batched_only(args):
+    """Just the batched varlen CTR workload at --batch-msgs messages: --warmup
+    then --steps graph replays (the profiling entry for the batch kernel)."""
+    import torch
+
+    from paper_1403_7295_gb300 import aes as A
+    from paper_1403_7295_gb300 import batch as B
+    from paper_1403_7295_gb300 import build as BLD
+    from synth import workloads as W
+
+    BLD.build()
+    A.lib()
+    wl = W.batched_varlen(3, args.batch_msgs)
+    lengths = wl["lengths"]
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(3, synth.STREAM_DATA, total, device="cuda")
+    b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=wl["key_bits"], ivs=wl["ivs"])
+    b.capture(B.AesBatchConfig(1024, 32768, 0, 0))
+    ms = time_graph(torch, b, args.steps) if args.warmup >= 3 else time_device(torch, b.replay, args.steps, args.warmup)
+    gbps = b.total_input_bytes() * args.steps / (ms / 1e3) / 1e9
+    print(json.dumps({"workload": f"batched varlen CTR, {args.batch_msgs} messages", "bytes": b.total_input_bytes(),
+                      "gbps": round(gbps, 1), "ms_per_batch": round(ms / args.steps, 3)}), flush=True)
 
 
 def batched_arm(torch, A, ctr128_gbps):
@@ -438,6 +474,39 @@ def batched_arm(torch, A, ctr128_gbps):
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
     }
     return out
+
+
+def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
+    """Continuous-batching server: Poisson arrivals at `rate`/s for `seconds`,
+    sizes 70 % 1-16 KiB / 25 % 16 KiB-1 MiB / 5 % 1-64 MiB, AES-256 CTR with
+    1,024 resident tenant schedules, 8 GiB admission budget, inputs sliced
+    from a 2 GiB device pool; p50/p99 of arrival -> completion."""
+    from paper_1403_7295_gb300.serve import Server
+    from synth import workloads as W
+
+    pool_bytes = 2 << 30
+    pool = synth.bytes_torch(5, synth.STREAM_DATA, pool_bytes, device="cuda")
+    n_t = 1024
+    keys = W.message_keys(5, n_t)
+    bits = np.full(n_t, 256, dtype=np.uint32)
+    nonces = synth.bytes_np(5, synth.STREAM_NONCE, 12 * n_t).reshape(n_t, 12)
+    arr = W.poisson_arrivals(5, rate, seconds)
+    n = arr.size
+    lengths = W.serving_sizes(5, n)
+    u = synth.uniform01(5, synth.STREAM_MISC + 3, n)
+    offs = (np.floor(u * (pool_bytes - lengths.astype(np.float64))).astype(np.uint64) // 16) * 16
+    tenants = W.tenants(5, n, n_t)
+    srv = Server(pool, keys, bits, nonces, budget_bytes=8 << 30, n_streams=2, slots_per_stream=2,
+                 max_batch_msgs=8192)
+    rep = srv.run(arr, tenants, offs, lengths, time_limit=seconds + 120.0)
+    rep.update({"rate_per_s": rate, "seconds": seconds, "key_bits": 256, "tenants": n_t,
+                "budget_bytes": 8 << 30, "offered_gbps": float(lengths.sum()) / seconds / 1e9})
+    for k in ("p50_ms", "p99_ms", "max_ms", "gbps", "wall_s", "mean_batch_msgs", "offered_gbps"):
+        if rep.get(k) is not None:
+            rep[k] = round(rep[k], 3)
+    del srv, pool
+    torch.cuda.empty_cache()
+    return rep
 
 
 def sweep(torch, A):
