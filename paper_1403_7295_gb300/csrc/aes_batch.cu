@@ -40,14 +40,19 @@ struct WindowSize<kBatchEcbDec> {
   static constexpr int value = 96;
 };
 
+// One message of the current window.  Its round keys live in the schedule
+// slot rk[0 .. 4(nr+1)); for CTR, words 60..63 hold the folded round-1
+// columns and word 64 the round-0 key word 3.
 struct Slot {
   uint64_t blk_start;  // global index of the message's first block
   uint64_t blk_end;
-  uint64_t in_off, out_off, len;
+  uint64_t full_end;   // first global block that is not a whole 16-byte input block
+  uint64_t src0, dst0; // byte address of (virtual) global block 0 of this message
   uint32_t nr, msg;
-  uint32_t c1[4];
-  uint32_t rk0w3, ctr0;
+  uint32_t rem;        // len mod 16
+  uint32_t ctr_base;   // CTR: counter of global block g is ctr_base + (uint32)g
 };
+constexpr uint32_t kCtrC1 = 60, kCtrRk0w3 = 64;
 
 template <int OPB>
 constexpr size_t batch_table_bytes() {
@@ -298,7 +303,8 @@ __device__ __forceinline__ uint32_t state_byte(const State& s, uint32_t k) {
   return (w >> (8 * (k & 3))) & 0xFFu;
 }
 
-// Fill slot `t` of the window with message m: offsets, key schedule, CTR constants.
+// Fill a window slot with message m: block range, addresses, key schedule,
+// CTR constants.
 template <int OPB>
 __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uint32_t sb_off,
                           uint32_t m, Slot& sl, uint32_t* rk) {
@@ -307,9 +313,11 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
   sl.msg = m;
   sl.nr = 10;
   if (sl.blk_end == sl.blk_start) return;  // empty or rejected: never selected
-  sl.in_off = a.in_off[m];
-  sl.out_off = a.out_off[m];
-  sl.len = a.in_len[m];
+  const uint64_t len = a.in_len[m];
+  sl.rem = static_cast<uint32_t>(len & 15u);
+  sl.full_end = sl.blk_start + len / 16;
+  sl.src0 = reinterpret_cast<uint64_t>(a.in) + a.in_off[m] - 16 * sl.blk_start;
+  sl.dst0 = reinterpret_cast<uint64_t>(a.out) + a.out_off[m] - 16 * sl.blk_start;
   if (a.keys != nullptr) {
     const uint32_t bits = a.key_bits[m];
     const uint32_t nk = bits / 32, nr = nk + 6;
@@ -326,12 +334,12 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
   if (OPB == kBatchCtr) {
     const uint4 ivw = *reinterpret_cast<const uint4*>(a.iv + 16ull * m);
     const uint32_t iv_w[4] = {ivw.x, ivw.y, ivw.z, ivw.w};
-    sl.ctr0 = __byte_perm(ivw.w, 0, 0x0123);
+    sl.ctr_base = __byte_perm(ivw.w, 0, 0x0123) - static_cast<uint32_t>(sl.blk_start);
     uint32_t s[4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) s[c] = iv_w[c] ^ rk[c];
     s[3] = 0;  // the counter column: looked up per block
-    sl.rk0w3 = rk[3];
+    rk[kCtrRk0w3] = rk[3];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint32_t acc = rk[4 + j];
@@ -340,37 +348,65 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
       if (((j + 1) & 3) != 3) acc ^= T.t1(s[(j + 1) & 3]);
       if (((j + 2) & 3) != 3) acc ^= T.t2(s[(j + 2) & 3]);
       if (((j + 3) & 3) != 3) acc ^= T.t3(s[(j + 3) & 3]);
-      sl.c1[j] = acc;
+      rk[kCtrC1 + j] = acc;
     }
   }
 }
 
+// The message a thread is working in, cached in registers and rebased to the
+// tile: blocks t0 + [s, e) of the tile belong to it, blocks below f are whole.
+struct Cur {
+  uint32_t s, e, f;
+  uint32_t nr;     // rounds | rem << 8 | (message ends in this tile) << 16
+  uint32_t ctr;    // counter of tile block 0 (CTR)
+  uint32_t slot;
+  uint64_t src, dst;  // byte address of tile block 0 in this message's input / output
+};
+
+__device__ __forceinline__ void select_message(const Slot* slots, uint32_t wn, uint64_t t0,
+                                               uint64_t t1, uint32_t gr, Cur& c) {
+  const uint64_t g = t0 + gr;
+  uint32_t lo = 0, hi = wn;  // last slot whose first block is <= g
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (slots[mid].blk_start <= g) lo = mid;
+    else hi = mid;
+  }
+  const Slot& sl = slots[lo];
+  const uint64_t bs = max(sl.blk_start, t0), be = min(sl.blk_end, t1);
+  const uint64_t bf = min(max(sl.full_end, t0), t1);
+  c.s = static_cast<uint32_t>(bs - t0);
+  c.e = static_cast<uint32_t>(be - t0);
+  c.f = static_cast<uint32_t>(bf - t0);
+  c.nr = sl.nr | (sl.rem << 8) | ((sl.blk_end <= t1 ? 1u : 0u) << 16);
+  c.ctr = sl.ctr_base + static_cast<uint32_t>(t0);
+  c.slot = lo;
+  c.src = sl.src0 + 16 * t0;
+  c.dst = sl.dst0 + 16 * t0;
+}
+
 template <int OPB>
-__device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T, const Slot& sl,
-                                              const uint32_t* rk, uint64_t g) {
-  const uint64_t j = g - sl.blk_start;
-  const uint64_t off = 16 * j;
-  const uint8_t* src = a.in + sl.in_off + off;
-  uint8_t* dst = a.out + sl.out_off + off;
-  const bool full = off + 16 <= sl.len;
+__device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T, const Slot* slots,
+                                              const uint32_t* rk, const Cur& c, uint32_t gr,
+                                              const uint4& v_in) {
+  const uint32_t nr = c.nr & 0xFFu, rem = (c.nr >> 8) & 0xFFu;
+  const bool full = gr < c.f;
+  const uint8_t* src = reinterpret_cast<const uint8_t*>(c.src + 16ull * gr);
+  uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst + 16ull * gr);
   if (OPB == kBatchCtr) {
-    const uint32_t ctr = sl.ctr0 + static_cast<uint32_t>(j);
-    const uint32_t x = __byte_perm(ctr, 0, 0x0123) ^ sl.rk0w3;
-    State s{sl.c1[0] ^ T.t3(x), sl.c1[1] ^ T.t2(x), sl.c1[2] ^ T.t1(x), sl.c1[3] ^ T.t0(x)};
-    s = enc_any(T, s, rk, sl.nr, 2);
+    const uint32_t x = __byte_perm(c.ctr + gr, 0, 0x0123) ^ rk[kCtrRk0w3];
+    const uint4 c1 = lds128(rk + kCtrC1);
+    State s{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
+    s = enc_any(T, s, rk, nr, 2);
     if (full) {
-      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src));
-      __stcs(reinterpret_cast<uint4*>(dst), make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3));
-    } else {
-      const uint32_t rem = static_cast<uint32_t>(sl.len - off);
+      __stcs(reinterpret_cast<uint4*>(dst),
+             make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3));
+    } else {  // partial last block: its leading `rem` bytes
       for (uint32_t b = 0; b < rem; ++b) dst[b] = src[b] ^ static_cast<uint8_t>(state_byte(s, b));
     }
   } else if (OPB == kBatchEcbEnc) {
-    uint4 v;
-    if (full) {
-      v = __ldcs(reinterpret_cast<const uint4*>(src));
-    } else {  // last block: rem message bytes then PKCS#7 pad bytes (1..16 of value 16 - rem)
-      const uint32_t rem = static_cast<uint32_t>(sl.len - off);
+    uint4 v = v_in;
+    if (!full) {  // last block: rem message bytes then PKCS#7 pad bytes (1..16 of value 16 - rem)
       const uint32_t pad = 16 - rem;
       uint32_t w[4];
       for (int q = 0; q < 4; ++q) {
@@ -386,21 +422,42 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
     }
     const uint4 k0 = lds128(rk);
     State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-    s = enc_any(T, s, rk, sl.nr, 1);
+    s = enc_any(T, s, rk, nr, 1);
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
   } else {
-    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src));
     const uint4 k0 = lds128(rk);
-    State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-    s = dec_any(T, s, rk, sl.nr);
+    State s{v_in.x ^ k0.x, v_in.y ^ k0.y, v_in.z ^ k0.z, v_in.w ^ k0.w};
+    s = dec_any(T, s, rk, nr);
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
-    if (g + 1 == sl.blk_end) {  // last block: check PKCS#7
+    if ((c.nr >> 16) && gr + 1 == c.e) {  // the message's last block: check PKCS#7
+      const Slot& sl = slots[c.slot];
       const uint32_t p = state_byte(s, 15);
       bool ok = p >= 1 && p <= 16;
       for (uint32_t k = 16 - (ok ? p : 0); k < 16; ++k) ok = ok && state_byte(s, k) == p;
       if (a.status) a.status[sl.msg] = ok ? AES_OK : AES_ERR_PADDING;
-      if (a.out_len) a.out_len[sl.msg] = ok ? sl.len - p : 0;
+      if (a.out_len) a.out_len[sl.msg] = ok ? 16 * (sl.blk_end - sl.blk_start) - p : 0;
     }
+  }
+}
+
+// Warp 0: claim the next tile and find its first and last message.
+__device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total,
+                                           unsigned long long* s_tile, uint32_t* s_mlo,
+                                           uint32_t* s_mhi) {
+  const uint32_t lane = threadIdx.x & 31;
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(a.tile_counter, 1ull);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  const uint64_t t0 = t * a.tile_blocks;
+  uint32_t mlo = 0, mhi = 0;
+  if (t0 < total) {
+    mlo = warp_find(a.blk_off, a.n, t0);
+    mhi = warp_find(a.blk_off, a.n, min(t0 + a.tile_blocks, total) - 1);
+  }
+  if (lane == 0) {
+    *s_tile = t;
+    *s_mlo = mlo;
+    *s_mhi = mhi;
   }
 }
 
@@ -412,55 +469,55 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
   __shared__ unsigned long long s_tile;
   __shared__ uint32_t s_mlo, s_mhi;
 
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t total = a.blk_off[a.n];
+  if (warp == 0) claim_tile(a, total, &s_tile, &s_mlo, &s_mhi);  // overlaps the table fill
+
   fill_tables<kDec>(smem);
   if (kDec) {  // forward S-box (all four bytes) beside the inverse one, for key expansion
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     for (int x = warp; x < 256; x += nwarps)
       smem[kRegionC / 4 + x * 64 + 32 + lane] = kDevTables.sbox[x] * 0x01010101u;
   }
   uint32_t* rk_all = smem + batch_table_bytes<OPB>() / 4;
   Slot* slots = reinterpret_cast<Slot*>(rk_all + kWin * kRkStride);
-  __syncthreads();
 
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const char* base = reinterpret_cast<const char*>(smem);
   const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
   // S-box source for key expansion: byte 0 of te2 (encryption tables) or the
   // forward S-box words in the upper half of region C (decryption tables).
   const char* sb = kDec ? T.c : T.b;
   const uint32_t sb_off = kDec ? T.hi : T.lo;
+  // Window slots are loaded by warps 1.. first, so warp 0 can look ahead.
+  const uint32_t first_slot = tid >= 32 ? tid - 32 : tid + blockDim.x - 32;
 
-  const uint64_t total = a.blk_off[a.n];
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1ull);
-    __syncthreads();
+    __syncthreads();  // the claimed tile is visible (and, first time, the tables)
     const uint64_t t0 = s_tile * a.tile_blocks;
+    const uint32_t m_lo = s_mlo, m_hi = s_mhi;
+    __syncthreads();  // everyone has read it before warp 0 claims the next one
     if (t0 >= total) break;
     const uint64_t t1 = min(t0 + a.tile_blocks, total);
-    if (warp == 0) {
-      const uint32_t m = warp_find(a.blk_off, a.n, t0);
-      if (lane == 0) s_mlo = m;
-    } else if (warp == 1) {
-      const uint32_t m = warp_find(a.blk_off, a.n, t1 - 1);
-      if (lane == 0) s_mhi = m;
-    }
-    __syncthreads();
-    const uint32_t m_lo = s_mlo, m_hi = s_mhi;
     for (uint32_t w0 = m_lo; w0 <= m_hi; w0 += kWin) {
       const uint32_t wn = min(static_cast<uint32_t>(kWin), m_hi - w0 + 1);
-      if (tid < wn) load_slot<OPB>(a, T, sb, sb_off, w0 + tid, slots[tid], rk_all + tid * kRkStride);
+      if (w0 == m_lo && warp == 0) claim_tile(a, total, &s_tile, &s_mlo, &s_mhi);
+      for (uint32_t sl = first_slot; sl < wn; sl += blockDim.x)
+        load_slot<OPB>(a, T, sb, sb_off, w0 + sl, slots[sl], rk_all + sl * kRkStride);
       __syncthreads();
-      const uint64_t g0 = max(t0, slots[0].blk_start);
-      const uint64_t g1 = min(t1, slots[wn - 1].blk_end);
-      for (uint64_t g = g0 + tid; g < g1; g += blockDim.x) {
-        // slot of block g: last slot whose first block is <= g
-        uint32_t lo = 0, hi = wn;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (slots[mid].blk_start <= g) lo = mid;
-          else hi = mid;
-        }
-        process_block<OPB>(a, T, slots[lo], rk_all + lo * kRkStride, g);
+      const uint32_t gr0 = static_cast<uint32_t>(max(t0, slots[0].blk_start) - t0);
+      const uint32_t gr1 = static_cast<uint32_t>(min(t1, slots[wn - 1].blk_end) - t0);
+      Cur c{1, 0, 0, 0, 0, 0, 0, 0};  // empty: the first block selects its message
+      uint4 next = make_uint4(0, 0, 0, 0);
+      bool have_next = false;
+      for (uint32_t gr = gr0 + tid; gr < gr1; gr += blockDim.x) {
+        if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
+        uint4 v = next;
+        if (!have_next && gr < c.f) v = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
+        // load the next block of the same message before this one's rounds
+        const uint32_t gn = gr + blockDim.x;
+        have_next = gn < gr1 && gn < c.f;
+        if (have_next) next = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gn));
+        process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v);
       }
       __syncthreads();
     }
