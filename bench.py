@@ -58,6 +58,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-probes", action="store_true")
+    p.add_argument("--no-variants", action="store_true", help="skip the T-table vs bitsliced comparison")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-message workloads")
     p.add_argument("--only", choices=["all", "batched"], default="all",
                    help="'batched': time only the batched varlen workload (for profiling)")
@@ -311,6 +312,8 @@ def gpu_arm(args):
                              "paper_best_cpu": "6637 Mb/s, pthreads, 4x Xeon X7560 (Table I)"}
         if not args.no_e2e:
             result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
+        if not args.no_variants:
+            result["variants"] = variant_arm(torch, A, args, ks, iv, x, y, value)
         if args.sweep:
             result["sweep"] = sweep(torch, A)
         if not args.no_batch:
@@ -352,6 +355,17 @@ def read_traffic(args):
     if per_gib is None:
         return None
     return per_gib * (args.size_mib / 1024)
+
+
+def variant_arm(torch, A, args, ks, iv, x, y, ttable_gbps):
+    """The two round implementations on the headline workload: the library's
+    choice (T-tables) against the bitsliced circuit."""
+    cfg = dict(variant=2, cta_threads=0, blocks_per_thread=0, grid_ctas=0)
+    steps = max(10, args.steps // 10)
+    ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), steps, 3)
+    bs = x.numel() * steps / (ms / 1e3) / 1e9
+    return {"ttable_gbps": round(ttable_gbps, 1), "bitslice_gbps": round(bs, 1),
+            "chosen": "ttable" if ttable_gbps >= bs else "bitslice"}
 
 
 def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):

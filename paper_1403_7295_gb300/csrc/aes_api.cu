@@ -112,6 +112,13 @@ aes_status resolve_shape(Op op, int nr, uint64_t nblocks, const aes_launch_confi
                          LaunchShape* shape) {
   const Defaults d = default_shape(op, nr);
   int variant = cfg ? cfg->variant : AES_VARIANT_AUTO;
+  if (variant == AES_VARIANT_BITSLICE) {
+    // fixed CTA shape (16 blocks per thread); grid 0 = as many CTAs as fit per SM
+    const int grid = cfg ? cfg->grid_ctas : 0;
+    if (grid < 0) return AES_ERR_ARG;
+    *shape = LaunchShape{kBitsliceThreads, 16, grid};
+    return AES_OK;
+  }
   if (variant != AES_VARIANT_AUTO && variant != AES_VARIANT_TTABLE) return AES_ERR_ARG;
   int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : d.cta_threads;
   int bpt = (cfg && cfg->blocks_per_thread) ? cfg->blocks_per_thread : d.blocks_per_thread;
@@ -177,13 +184,20 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
   LaunchShape shape{};
   s = resolve_shape(op, static_cast<int>(ks->nr), nblocks, cfg, &shape);
   if (s != AES_OK) return s;
+  const bool bitslice = cfg && cfg->variant == AES_VARIANT_BITSLICE;
   RoundKeys rk;
-  copy_round_keys(op == Op::kEcbDecrypt ? ks->rk_dec : ks->rk_enc, static_cast<int>(ks->nr), &rk);
+  copy_round_keys(op == Op::kEcbDecrypt && !bitslice ? ks->rk_dec : ks->rk_enc,
+                  static_cast<int>(ks->nr), &rk);
   CtrParams cp{};
   if (op == Op::kCtr) cp = make_ctr_params(ks, iv);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int nr = static_cast<int>(ks->nr);
   cudaError_t e = cudaSuccess;
+  if (bitslice) {
+    e = launch_bitslice(op, nr, din, dout, nblocks, tail, rk, cp, shape, st);
+    if (e != cudaSuccess) return cuda_failure(e);
+    return AES_OK;
+  }
   switch (op) {
     case Op::kEcbEncrypt: e = launch_ttable_enc(nr, din, dout, nblocks, 0, rk, cp, shape, st); break;
     case Op::kEcbDecrypt: e = launch_ttable_dec(nr, din, dout, nblocks, 0, rk, cp, shape, st); break;

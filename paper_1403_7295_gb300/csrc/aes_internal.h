@@ -42,6 +42,14 @@ AESGPU_DECLARE_LAUNCH(launch_ttable_dec)
 AESGPU_DECLARE_LAUNCH(launch_ttable_ctr)
 #undef AESGPU_DECLARE_LAUNCH
 
+// Bitsliced launches (32 blocks per thread, 128-thread CTAs).  Decryption takes
+// the encryption schedule (plain InvCipher order).
+cudaError_t launch_bitslice(Op op, int nr, const void* in, void* out, uint64_t nblocks,
+                            uint32_t tail_bytes, const RoundKeys& rk, const CtrParams& cp,
+                            const LaunchShape& shape, cudaStream_t stream);
+constexpr int kBitsliceThreads = 128;
+constexpr int kBitsliceBlocksPerCta = 4 * 512;  // 4 warps x 512 blocks per iteration
+
 // Dynamic shared memory of the T-table kernels (bytes).
 constexpr int kTtableSmemEnc = 128 * 1024;
 constexpr int kTtableSmemDec = 192 * 1024;

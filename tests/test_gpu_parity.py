@@ -26,6 +26,8 @@ SHAPES = [
     dict(variant=1, cta_threads=512, blocks_per_thread=4, grid_ctas=7),
     dict(variant=1, cta_threads=1024, blocks_per_thread=4, grid_ctas=0),
     dict(variant=1, cta_threads=1024, blocks_per_thread=1, grid_ctas=1),
+    dict(variant=2, cta_threads=0, blocks_per_thread=0, grid_ctas=0),  # bitsliced
+    dict(variant=2, cta_threads=0, blocks_per_thread=0, grid_ctas=3),
 ]
 
 
