@@ -303,6 +303,11 @@ def gpu_arm(args):
             peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
             rl["peak"] = round(peak, 1)
             rl["frac"] = round(g_lookups / peak, 4)
+            measured = read_profile_field(args, "lookups_per_block_measured:")
+            if measured:
+                # the kernel's own lookups (CTR caching does fewer than 16*Nr): how busy the pipe is
+                rl["lookups_per_block_measured"] = measured
+                rl["pipe_frac"] = round(measured * blocks / per_launch_s / 1e9 / peak, 4)
             rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
                                  f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
         result["roofline"] = rl
@@ -335,13 +340,32 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def read_profile_field(args, key):
+    """A number from the committed ncu summary of the default kernel, if the
+    summary still matches the kernel source and this run uses that kernel."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ttable_ctr_aes128_1GiB.md")
+    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128 or args.bpt or args.variant:
+        return None
+    src = os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", "aes_ttable.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(path).read()
+    if f"source_sha256_16: {sha}" not in text:
+        return None
+    for ln in text.splitlines():
+        if ln.startswith(key):
+            return float(ln.split()[1])
+    return None
+
+
 def read_traffic(args):
     """dram bytes per launch from the committed ncu summary, if it still
     matches the kernel source; else null."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "ttable_ctr_aes128_1GiB.md")
-    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128:
+    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128 or args.bpt or args.variant:
         return None
     src = os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", "aes_ttable.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

@@ -74,7 +74,9 @@ typedef enum aes_variant {
 typedef struct aes_launch_config {
     int32_t variant;           /* aes_variant */
     int32_t cta_threads;       /* threads per CTA: 128..1024, multiple of 32 */
-    int32_t blocks_per_thread; /* 16-byte blocks per thread per iteration: 1, 2 or 4 */
+    int32_t blocks_per_thread; /* 16-byte blocks per thread per iteration: 1, 2 or 4; 0 = the
+                                  library choice (for CTR: the run-cached kernel, which walks
+                                  256 consecutive counters per warp and caches two rounds) */
     int32_t grid_ctas;         /* CTAs in the grid; 0 = one per SM */
 } aes_launch_config;
 

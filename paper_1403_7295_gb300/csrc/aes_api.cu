@@ -98,14 +98,14 @@ int sm_count() {
 struct Defaults {
   int cta_threads, blocks_per_thread;
 };
+// blocks_per_thread 0 selects the run-cached CTR kernel (two cached rounds).
 Defaults default_shape(Op op, int nr) {
-  (void)nr;
   switch (op) {
-    case Op::kCtr: return {1024, 2};
-    case Op::kEcbEncrypt: return {1024, 2};
-    case Op::kEcbDecrypt: return {1024, 2};
+    case Op::kCtr: return {1024, 0};
+    case Op::kEcbEncrypt:
+    case Op::kEcbDecrypt: return {1024, nr == 10 ? 4 : 1};
   }
-  return {1024, 2};
+  return {1024, 1};
 }
 
 aes_status resolve_shape(Op op, int nr, uint64_t nblocks, const aes_launch_config* cfg,
@@ -123,9 +123,13 @@ aes_status resolve_shape(Op op, int nr, uint64_t nblocks, const aes_launch_confi
   int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : d.cta_threads;
   int bpt = (cfg && cfg->blocks_per_thread) ? cfg->blocks_per_thread : d.blocks_per_thread;
   if (cta < 128 || cta > 1024 || cta % 32 != 0) return AES_ERR_ARG;
-  if (bpt != 1 && bpt != 2 && bpt != 4) return AES_ERR_ARG;
+  if (bpt != 1 && bpt != 2 && bpt != 4 && !(bpt == 0 && op == Op::kCtr)) return AES_ERR_ARG;
   int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
   if (grid < 0) return AES_ERR_ARG;
+  if (bpt == 0) {  // the cached CTR kernel sizes its own grid from the runs
+    *shape = LaunchShape{cta, 0, grid};
+    return AES_OK;
+  }
   // No more CTAs than there is work for (at least one, for a tail-only call).
   const uint64_t per_cta = static_cast<uint64_t>(cta) * bpt;
   const uint64_t needed = nblocks == 0 ? 1 : (nblocks + per_cta - 1) / per_cta;

@@ -208,6 +208,85 @@ __global__ void __launch_bounds__(1024, 1)
   }
 }
 
+// CTR with two cached rounds.  Counters that share their upper 24 bits
+// (a run of 256 aligned counters) give the same state columns 1..3 after
+// round 1 (only the counter's low byte, in column 0 of the round-1 output,
+// changes), so 12 of round 2's 16 lookups are the same for the whole run.
+// A warp walks one such run at a time, lane l taking counters 32k + l
+// (k = 0..7, coalesced 512-byte accesses per k); each lane computes the run's
+// constants once (3 + 12 lookups) and then spends 1 + 4 lookups per block on
+// rounds 1-2 instead of 4 + 16.
+template <int NR>
+__global__ void __launch_bounds__(1024, 1)
+    ttable_ctr_cached_kernel(const uint4* in, uint4* out, uint64_t nblocks, uint32_t tail_bytes,
+                             const __grid_constant__ RoundKeys rk,
+                             const __grid_constant__ CtrParams cp) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<false>(smem);
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31;
+  const char* base = reinterpret_cast<const char*>(smem);
+  const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
+
+  const uint32_t off0 = cp.ctr0 & 255u;  // position of block 0 inside its run
+  const uint64_t units = nblocks + (tail_bytes ? 1 : 0);
+  const uint64_t runs = (units + off0 + 255) / 256;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t run = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       run < runs; run += warps) {
+    // counter of position 0 of this run (modulo 2^32); its low byte is 0
+    const uint32_t ctr_run = (cp.ctr0 & ~255u) + static_cast<uint32_t>(run) * 256u;
+    const uint32_t xr = __byte_perm(ctr_run, 0, 0x0123) ^ cp.rk0w3;  // byte 3 still to add
+    const uint32_t s1 = cp.c1[1] ^ T.t2(xr), s2 = cp.c1[2] ^ T.t1(xr), s3 = cp.c1[3] ^ T.t0(xr);
+    const uint32_t d0 = rk.w[8] ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
+    const uint32_t d1 = rk.w[9] ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
+    const uint32_t d2 = rk.w[10] ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
+    const uint32_t d3 = rk.w[11] ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
+    const int64_t first = static_cast<int64_t>(run) * 256 - off0;  // block index of position 0
+#pragma unroll 2
+    for (uint32_t k = 0; k < 8; ++k) {
+      const uint32_t t = 32 * k + lane;
+      const int64_t idx = first + t;
+      if (idx < 0 || static_cast<uint64_t>(idx) >= units) continue;
+      const bool full = static_cast<uint64_t>(idx) < nblocks;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (full) v = __ldcs(in + idx);
+      const uint32_t s0 = cp.c1[0] ^ T.t3(xr ^ (t << 24));
+      State s{d0 ^ T.t0(s0), d1 ^ T.t3(s0), d2 ^ T.t2(s0), d3 ^ T.t1(s0)};
+      encrypt_rounds<NR>(T, s, rk, 3);
+      if (full) {
+        __stcs(out + idx, xor4(v, s));
+      } else {  // partial last block: its leading keystream bytes
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
+        uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
+        for (uint32_t b = 0; b < tail_bytes; ++b) {
+          const uint32_t w = b < 4 ? s.s0 : b < 8 ? s.s1 : b < 12 ? s.s2 : s.s3;
+          dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
+        }
+      }
+    }
+  }
+}
+
+template <int NR>
+cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                              const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                              cudaStream_t stream) {
+  auto kern = ttable_ctr_cached_kernel<NR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kTtableSmemEnc);
+  if (e != cudaSuccess) return e;
+  // one warp per run of 256 blocks: no more CTAs than runs / warps per CTA
+  const uint64_t runs = (nblocks + (tail ? 1 : 0) + (cp.ctr0 & 255u) + 255) / 256;
+  const uint64_t warps_per_cta = shape.cta_threads / 32;
+  uint64_t grid = shape.grid_ctas;
+  const uint64_t needed = (runs + warps_per_cta - 1) / warps_per_cta;
+  if (grid > needed) grid = needed > 0 ? needed : 1;
+  kern<<<static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream>>>(
+      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
+  return cudaGetLastError();
+}
+
 template <Op OP, int NR, int BPT>
 cudaError_t launch_one(const void* in, void* out, uint64_t nblocks, uint32_t tail,
                        const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
@@ -226,6 +305,10 @@ template <Op OP, int NR>
 cudaError_t dispatch_bpt(const void* in, void* out, uint64_t nblocks, uint32_t tail,
                          const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
                          cudaStream_t stream) {
+  if constexpr (OP == Op::kCtr) {
+    if (shape.blocks_per_thread == 0)  // the run-cached CTR kernel
+      return launch_ctr_cached<NR>(in, out, nblocks, tail, rk, cp, shape, stream);
+  }
   switch (shape.blocks_per_thread) {
     case 1: return launch_one<OP, NR, 1>(in, out, nblocks, tail, rk, cp, shape, stream);
     case 2: return launch_one<OP, NR, 2>(in, out, nblocks, tail, rk, cp, shape, stream);
