@@ -208,22 +208,39 @@ __device__ __forceinline__ uint32_t load_le32(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// FIPS-197 §5.2 into rk[0 .. 4(nr+1)).  key: 4-byte aligned, nk words.
-__device__ void expand_key(const Tabs& T, const char* sb, uint32_t sb_off, const uint8_t* key,
-                           uint32_t nk, uint32_t nr, uint32_t* rk) {
-  for (uint32_t i = 0; i < nk; ++i) rk[i] = load_le32(key + 4 * i);
+// FIPS-197 §5.2 into rk[0 .. 4(nr+1)).  key: 4-byte aligned, NK words.  The
+// last NK words live in registers (w[i mod NK]), so the dependency chain has
+// no shared-memory round trips; rk[] is only written.
+template <int NK>
+__device__ __forceinline__ void expand_key_nk(const Tabs& T, const char* sb, uint32_t sb_off,
+                                              const uint8_t* key, uint32_t* rk) {
+  constexpr int kWords = 4 * (NK + 7);
+  uint32_t w[NK];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    w[i] = load_le32(key + 4 * i);
+    rk[i] = w[i];
+  }
   uint32_t rcon = 1;
-  const uint32_t nwords = 4 * (nr + 1);
-  for (uint32_t i = nk; i < nwords; ++i) {
-    uint32_t t = rk[i - 1];
-    if (i % nk == 0) {
+#pragma unroll
+  for (int i = NK; i < kWords; ++i) {
+    uint32_t t = w[(i - 1) % NK];
+    if (i % NK == 0) {
       t = sub_word(T, sb, sb_off, __funnelshift_r(t, t, 8)) ^ rcon;  // RotWord, SubWord, Rcon
       rcon = ((rcon << 1) ^ ((rcon & 0x80u) ? 0x1Bu : 0u)) & 0xFFu;
-    } else if (nk == 8 && i % nk == 4) {
+    } else if (NK == 8 && i % NK == 4) {
       t = sub_word(T, sb, sb_off, t);
     }
-    rk[i] = rk[i - nk] ^ t;
+    w[i % NK] ^= t;  // w[i] = w[i - NK] ^ t
+    rk[i] = w[i % NK];
   }
+}
+
+__device__ void expand_key(const Tabs& T, const char* sb, uint32_t sb_off, const uint8_t* key,
+                           uint32_t nk, uint32_t* rk) {
+  if (nk == 4) expand_key_nk<4>(T, sb, sb_off, key, rk);
+  else if (nk == 6) expand_key_nk<6>(T, sb, sb_off, key, rk);
+  else expand_key_nk<8>(T, sb, sb_off, key, rk);
 }
 
 // Turn an encryption schedule into the equivalent inverse cipher's (FIPS-197
@@ -322,7 +339,7 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
     const uint32_t bits = a.key_bits[m];
     const uint32_t nk = bits / 32, nr = nk + 6;
     sl.nr = nr;
-    expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, nr, rk);
+    expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, rk);
     if (OPB == kBatchEcbDec) to_decrypt_schedule(T, sb, sb_off, nr, rk);
   } else {
     const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
@@ -378,26 +395,58 @@ __device__ __forceinline__ void select_message(const Slot* slots, uint32_t wn, u
   c.s = static_cast<uint32_t>(bs - t0);
   c.e = static_cast<uint32_t>(be - t0);
   c.f = static_cast<uint32_t>(bf - t0);
-  c.nr = sl.nr | (sl.rem << 8) | ((sl.blk_end <= t1 ? 1u : 0u) << 16);
+  // bit 17: long message (>= 512 blocks): CTR caches counter runs for it
+  c.nr = sl.nr | (sl.rem << 8) | ((sl.blk_end <= t1 ? 1u : 0u) << 16) |
+         ((sl.blk_end - sl.blk_start >= 512 ? 1u : 0u) << 17);
   c.ctr = sl.ctr_base + static_cast<uint32_t>(t0);
   c.slot = lo;
   c.src = sl.src0 + 16 * t0;
   c.dst = sl.dst0 + 16 * t0;
 }
 
+// Per-thread cache of one CTR counter run (256 aligned counters of one
+// message): after round 1 only column 0 depends on the counter's low byte,
+// so round 2 is d_j ^ (one lookup) for the whole run.
+struct RunCache {
+  uint32_t run, slot;    // counter >> 8 and window slot + 1 (0: empty)
+  uint32_t xr, c10;      // counter word of the run start ^ rk0 word 3; folded round-1 column 0
+  uint32_t d0, d1, d2, d3;
+};
+
 template <int OPB>
 __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T, const Slot* slots,
                                               const uint32_t* rk, const Cur& c, uint32_t gr,
-                                              const uint4& v_in) {
+                                              const uint4& v_in, RunCache& rc) {
   const uint32_t nr = c.nr & 0xFFu, rem = (c.nr >> 8) & 0xFFu;
   const bool full = gr < c.f;
   const uint8_t* src = reinterpret_cast<const uint8_t*>(c.src + 16ull * gr);
   uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst + 16ull * gr);
   if (OPB == kBatchCtr) {
-    const uint32_t x = __byte_perm(c.ctr + gr, 0, 0x0123) ^ rk[kCtrRk0w3];
-    const uint4 c1 = lds128(rk + kCtrC1);
-    State s{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
-    s = enc_any(T, s, rk, nr, 2);
+    const uint32_t ctr = c.ctr + gr;
+    State s;
+    if (!((c.nr >> 17) & 1u)) {  // short message: round 1 folded per message, rounds 2.. in full
+      const uint32_t x = __byte_perm(ctr, 0, 0x0123) ^ rk[kCtrRk0w3];
+      const uint4 c1 = lds128(rk + kCtrC1);
+      s = State{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
+      s = enc_any(T, s, rk, nr, 2);
+    } else {
+    if ((ctr >> 8) != rc.run || c.slot + 1 != rc.slot) {  // a new run: its round-1/2 constants
+      rc.run = ctr >> 8;
+      rc.slot = c.slot + 1;
+      rc.xr = __byte_perm(ctr & ~255u, 0, 0x0123) ^ rk[kCtrRk0w3];
+      const uint4 c1 = lds128(rk + kCtrC1);
+      rc.c10 = c1.x;
+      const uint32_t s1 = c1.y ^ T.t2(rc.xr), s2 = c1.z ^ T.t1(rc.xr), s3 = c1.w ^ T.t0(rc.xr);
+      const uint4 k2 = lds128(rk + 8);
+      rc.d0 = k2.x ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
+      rc.d1 = k2.y ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
+      rc.d2 = k2.z ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
+      rc.d3 = k2.w ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
+    }
+    const uint32_t s0 = rc.c10 ^ T.t3(rc.xr ^ ((ctr & 255u) << 24));
+    s = State{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
+    s = enc_any(T, s, rk, nr, 3);
+    }
     if (full) {
       __stcs(reinterpret_cast<uint4*>(dst),
              make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3));
@@ -429,7 +478,7 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
     State s{v_in.x ^ k0.x, v_in.y ^ k0.y, v_in.z ^ k0.z, v_in.w ^ k0.w};
     s = dec_any(T, s, rk, nr);
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
-    if ((c.nr >> 16) && gr + 1 == c.e) {  // the message's last block: check PKCS#7
+    if (((c.nr >> 16) & 1u) && gr + 1 == c.e) {  // the message's last block: check PKCS#7
       const Slot& sl = slots[c.slot];
       const uint32_t p = state_byte(s, 15);
       bool ok = p >= 1 && p <= 16;
@@ -466,12 +515,15 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
   constexpr int kWin = WindowSize<OPB>::value;
   constexpr bool kDec = OPB == kBatchEcbDec;
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ unsigned long long s_tile;
-  __shared__ uint32_t s_mlo, s_mhi;
+  // the claimed tile, double-buffered: tile i reads entry i & 1 while warp 0
+  // writes tile i + 1 into the other entry
+  __shared__ unsigned long long s_tile[2];
+  __shared__ uint32_t s_mlo[2], s_mhi[2];
+  __shared__ uint32_t s_span;  // next 256-block span of the current window
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.blk_off[a.n];
-  if (warp == 0) claim_tile(a, total, &s_tile, &s_mlo, &s_mhi);  // overlaps the table fill
+  if (warp == 0) claim_tile(a, total, &s_tile[0], &s_mlo[0], &s_mhi[0]);  // overlaps the table fill
 
   fill_tables<kDec>(smem);
   if (kDec) {  // forward S-box (all four bytes) beside the inverse one, for key expansion
@@ -491,33 +543,52 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
   // Window slots are loaded by warps 1.. first, so warp 0 can look ahead.
   const uint32_t first_slot = tid >= 32 ? tid - 32 : tid + blockDim.x - 32;
 
-  for (;;) {
-    __syncthreads();  // the claimed tile is visible (and, first time, the tables)
-    const uint64_t t0 = s_tile * a.tile_blocks;
-    const uint32_t m_lo = s_mlo, m_hi = s_mhi;
-    __syncthreads();  // everyone has read it before warp 0 claims the next one
+  for (uint32_t it = 0;; ++it) {
+    __syncthreads();  // tile `it` is visible (and, first time, the tables)
+    const uint32_t cur = it & 1;
+    const uint64_t t0 = s_tile[cur] * a.tile_blocks;
+    const uint32_t m_lo = s_mlo[cur], m_hi = s_mhi[cur];
     if (t0 >= total) break;
     const uint64_t t1 = min(t0 + a.tile_blocks, total);
     for (uint32_t w0 = m_lo; w0 <= m_hi; w0 += kWin) {
       const uint32_t wn = min(static_cast<uint32_t>(kWin), m_hi - w0 + 1);
-      if (w0 == m_lo && warp == 0) claim_tile(a, total, &s_tile, &s_mlo, &s_mhi);
       for (uint32_t sl = first_slot; sl < wn; sl += blockDim.x)
         load_slot<OPB>(a, T, sb, sb_off, w0 + sl, slots[sl], rk_all + sl * kRkStride);
+      if (tid == blockDim.x - 1) s_span = 0;
       __syncthreads();
+      // Look ahead while the others start on the window: warp 0 claims tile
+      // it + 1 into the other entry (last read before this tile's barrier)
+      // and joins the spans afterwards.
+      if (w0 == m_lo && warp == 0)
+        claim_tile(a, total, &s_tile[cur ^ 1], &s_mlo[cur ^ 1], &s_mhi[cur ^ 1]);
       const uint32_t gr0 = static_cast<uint32_t>(max(t0, slots[0].blk_start) - t0);
       const uint32_t gr1 = static_cast<uint32_t>(min(t1, slots[wn - 1].blk_end) - t0);
       Cur c{1, 0, 0, 0, 0, 0, 0, 0};  // empty: the first block selects its message
+      RunCache rc{0, 0, 0, 0, 0, 0, 0, 0};
       uint4 next = make_uint4(0, 0, 0, 0);
       bool have_next = false;
-      for (uint32_t gr = gr0 + tid; gr < gr1; gr += blockDim.x) {
-        if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
-        uint4 v = next;
-        if (!have_next && gr < c.f) v = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
-        // load the next block of the same message before this one's rounds
-        const uint32_t gn = gr + blockDim.x;
-        have_next = gn < gr1 && gn < c.f;
-        if (have_next) next = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gn));
-        process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v);
+      // Warps claim spans of 256 consecutive blocks from a shared counter (so
+      // they finish the window together); lane l takes blocks 32k + l of the
+      // span (coalesced), so a lane's blocks share counter runs.
+      for (;;) {
+        uint32_t sp = 0;
+        if (lane == 0) sp = atomicAdd(&s_span, 1u);
+        sp = __shfl_sync(0xffffffffu, sp, 0);
+        const uint32_t span = gr0 + sp * 256;
+        if (span >= gr1) break;
+        have_next = false;
+        for (uint32_t k = 0; k < 8; ++k) {
+          const uint32_t gr = span + 32 * k + lane;
+          if (gr >= gr1) break;
+          if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
+          uint4 v = next;
+          if (!have_next && gr < c.f) v = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
+          // load this lane's next block of the span (same message) before this one's rounds
+          const uint32_t gn = gr + 32;
+          have_next = k < 7 && gn < gr1 && gn < c.f;
+          if (have_next) next = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gn));
+          process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v, rc);
+        }
       }
       __syncthreads();
     }
