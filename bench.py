@@ -232,8 +232,12 @@ def gpu_arm(args):
     nbytes = args.size_mib << 20
     seed = rank
     bits = args.bits
-    key = synth.key_bytes(seed, bits)
-    iv = synth.iv_bytes(seed)
+    # Every rank holds one shard of a logical world x size buffer under one key:
+    # rank r's counter starts at its first block (the paper's chunk split, no exchange).
+    from paper_1403_7295_gb300.shard import ctr_iv_at
+
+    key = synth.key_bytes(0, bits)
+    iv = np.frombuffer(ctr_iv_at(synth.iv_bytes(0), rank * (nbytes // 16)), np.uint8)
     ks = A.aes_expand_key(key)
     x = synth.bytes_torch(seed, synth.STREAM_DATA, nbytes, device="cuda")
     y = torch.empty_like(x)
@@ -275,14 +279,15 @@ def gpu_arm(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u8",
-        "data": "synthetic: SplitMix64-seeded uniform random bytes, key and nonce per rank",
+        "data": "synthetic: SplitMix64-seeded uniform random bytes",
         "config": {
             "workload": f"AES-{bits} {args.mode.upper()} of one {args.size_mib} MiB buffer per GPU, "
                         "device-resident (single-buffer sweep, largest-buffer headline case)",
             "key_bits": bits, "mode": args.mode, "buffer_bytes": nbytes,
             "l2": "input larger than L2 (129 MB); no flush",
             "launch": cfg or "library default",
-            "parallelism": f"independent buffers x{world}",
+            "parallelism": f"{world} contiguous shards of one {world * args.size_mib} MiB buffer "
+                           "(one key, counter offset per shard, no data exchange)",
         },
         "gpu_launches": args.steps,
     }

@@ -146,7 +146,8 @@ class Server:
 
     def __init__(self, pool, tenant_keys: np.ndarray, tenant_bits: np.ndarray, tenant_nonces: np.ndarray,
                  budget_bytes: int = 8 << 30, n_streams: int = 2, slots_per_stream: int = 2,
-                 max_batch_msgs: int = 8192, grid_ctas: int = 0, device="cuda"):
+                 max_batch_msgs: int = 8192, grid_ctas: int = 0, batch_timeout_s: float = 10.0,
+                 device="cuda"):
         import torch
 
         self.torch = torch
@@ -176,6 +177,12 @@ class Server:
         self.next_stream = 0
         self.batches = []  # (t_launch, t_done, n_reqs, bytes, stream index)
         self.on_complete = None  # optional callback(request, out_view) at completion
+        # Bounded wait: a batch not complete after batch_timeout_s is declared
+        # lost; its requests fail with a timeout and its slot and output bytes
+        # are quarantined (never reused: the GPU might still write them).
+        self.batch_timeout_s = batch_timeout_s
+        self.timed_out: list[Request] = []
+        self.quarantined: list[_Slot] = []
 
     # ---- request flow ----
     def arrive(self, req: Request):
@@ -246,6 +253,13 @@ class Server:
         done = 0
         for slot in list(self.inflight):
             if not slot.event.query():
+                t = now_fn()
+                if t - slot.t_launch > self.batch_timeout_s:
+                    self.inflight.remove(slot)
+                    self.quarantined.append(slot)
+                    for r in slot.reqs:
+                        r.done = -2.0  # timed out
+                        self.timed_out.append(r)
                 continue
             t = now_fn()
             self.inflight.remove(slot)
@@ -266,6 +280,10 @@ class Server:
 
     def idle(self) -> bool:
         return not (self.waiting or self.admitted or self.inflight)
+
+    def healthy(self) -> bool:
+        """False once a batch has timed out: stop admitting and report."""
+        return not self.quarantined
 
     # ---- driving a recorded workload in real time ----
     def run(self, arrivals: np.ndarray, tenants: np.ndarray, in_offs: np.ndarray, lengths: np.ndarray,
@@ -288,12 +306,15 @@ class Server:
             while i < n and reqs[i].arrival <= now:
                 self.arrive(reqs[i])
                 i += 1
-            self.admit(now)
-            while self.launch(now):
-                pass
+            if self.healthy():
+                self.admit(now)
+                while self.launch(now):
+                    pass
             self.poll(now_fn)
             if i >= n and self.idle():
                 break
+            if not self.healthy() and not self.inflight:
+                break  # a batch was lost: report instead of waiting forever
             if now > limit:
                 break
         self.torch.cuda.synchronize()
@@ -322,4 +343,5 @@ class Server:
             "mean_batch_msgs": float(np.mean([x[2] for x in self.batches])) if self.batches else 0.0,
             "batches_launched_while_previous_in_flight": overlap,
             "max_budget_charged": int(self.max_charged), "budget": int(self.budget),
+            "timed_out": len(self.timed_out),
         }

@@ -125,3 +125,33 @@ def test_tenant_counters_never_reuse_a_keystream_block(torch):
         ranges = sorted((c, c + nb) for (tt, c, nb) in ivs.values() if tt == t)
         for (a0, a1), (b0, b1) in zip(ranges, ranges[1:]):
             assert a1 <= b0
+
+
+class _NeverDone:
+    """A completion event that never fires: a lost batch, injected on the host."""
+
+    def query(self):
+        return False
+
+
+def test_lost_batch_times_out_without_hanging(torch):
+    import time
+
+    from paper_1403_7295_gb300.serve import Request
+
+    srv, pool, keys, bits = setup_server(torch, 4, 16 << 20, 64 << 20, seed=80, batch_timeout_s=0.2)
+    srv.arrive(Request(0, 1, 0, 4096, 0.0))
+    srv.admit(0.0)
+    assert srv.launch(0.0)
+    slot = srv.inflight[0]
+    torch.cuda.synchronize()
+    slot.event = _NeverDone()  # the real work finished; the host never hears of it
+    t0 = time.perf_counter()
+    while srv.inflight and time.perf_counter() - t0 < 5.0:
+        srv.poll(lambda: time.perf_counter() - t0 + 0.0)
+    assert not srv.inflight and len(srv.timed_out) == 1 and not srv.healthy()
+    assert srv.quarantined and srv.quarantined[0] is slot
+    # the run loop stops admitting and returns instead of waiting forever
+    arr = np.array([0.0, 0.001])
+    rep = srv.run(arr, np.array([0, 1]), np.zeros(2, np.uint64), np.array([32, 32], np.uint64), time_limit=5.0)
+    assert rep["completed"] == 0 and rep["timed_out"] == 1
