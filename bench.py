@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--cta", type=int, default=0)
     p.add_argument("--bpt", type=int, default=0)
     p.add_argument("--sweep", action="store_true", help="also time the 36-run key/mode/size sweep")
+    p.add_argument("--scaling", action="store_true",
+                   help="also time throughput vs buffer size and vs CTAs (the paper's Figs. 4-9 on GPU)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-probes", action="store_true")
@@ -326,6 +328,8 @@ def gpu_arm(args):
             result["variants"] = variant_arm(torch, A, args, ks, iv, x, y, value)
         if args.sweep:
             result["sweep"] = sweep(torch, A)
+        if args.scaling:
+            result["scaling_study"] = scaling_study(torch, A)
         if not args.no_batch:
             del x, y
             torch.cuda.empty_cache()
@@ -571,6 +575,37 @@ def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
     del srv, pool
     torch.cuda.empty_cache()
     return rep
+
+
+def scaling_study(torch, A):
+    """The paper's throughput-vs-data-size and throughput-vs-parallel-instances
+    curves (its Figs. 4-9, on CPUs) restated for one GB300: AES-128 CTR GB/s
+    for buffers of 1 KiB .. 8 GiB, and for 1 .. all SMs' worth of CTAs on
+    1 GiB (one CTA per SM)."""
+    out = {"size_bytes": [], "size_gbps": [], "ctas": [], "ctas_gbps": []}
+    ks = A.aes_expand_key(synth.key_bytes(9, 128))
+    iv = synth.iv_bytes(9)
+    big = synth.bytes_torch(9, synth.STREAM_DATA, 8 << 30, device="cuda")
+    dst = torch.empty_like(big)
+    for lg in range(10, 34, 2):  # 1 KiB .. 8 GiB
+        n = 1 << lg
+        x, y = big[:n], dst[:n]
+        steps = int(min(2000, max(5, (4 << 30) // n)))
+        ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y), steps, 3)
+        out["size_bytes"].append(n)
+        out["size_gbps"].append(round(n * steps / (ms / 1e3) / 1e9, 2))
+    n = 1 << 30
+    x, y = big[:n], dst[:n]
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    for ctas in sorted({1, 2, 4, 8, 16, 32, 64, 96, 128, sms}):
+        cfg = dict(variant=1, cta_threads=0, blocks_per_thread=0, grid_ctas=ctas)
+        steps = max(3, min(50, 2 * ctas))
+        ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y, config=cfg), steps, 2)
+        out["ctas"].append(ctas)
+        out["ctas_gbps"].append(round(n * steps / (ms / 1e3) / 1e9, 2))
+    del big, dst
+    torch.cuda.empty_cache()
+    return out
 
 
 def sweep(torch, A):
