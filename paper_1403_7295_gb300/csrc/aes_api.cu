@@ -2,6 +2,7 @@
 // validation, launch-shape choice and dispatch to the round kernels.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "aes_batch.h"
@@ -87,11 +88,15 @@ aes_status check_buffers(const void* in, void* out, size_t nbytes, const void** 
   return AES_OK;
 }
 
+// SM count of the current device, looked up once per device ordinal.
 int sm_count() {
+  static std::atomic<int> cache[64];
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-  return n > 0 ? n : 1;
+  if (dev >= 0 && dev < 64 && (n = cache[dev].load(std::memory_order_relaxed)) > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
 }
 
 // Default launch shapes (measured on GB300; see the bench's autotune output).

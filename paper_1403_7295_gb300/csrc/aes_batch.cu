@@ -16,6 +16,7 @@
 //      decryption), then run the T-table rounds of aes_ttable.cuh with round
 //      keys read from shared memory (one 128-bit broadcast load per round).
 #include "aes_batch.h"
+#include "aes_smem_attr.h"
 #include "aes_ttable.cuh"
 
 namespace aesgpu {
@@ -600,8 +601,7 @@ cudaError_t launch_persistent(const BatchArgs& a, int cta, int grid, cudaStream_
   constexpr size_t smem = batch_smem_bytes<OPB>();
   static_assert(smem + 64 <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
   auto kern = batch_kernel<OPB>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = ensure_dynamic_smem(kern, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<grid, cta, smem, s>>>(a);
   return cudaGetLastError();

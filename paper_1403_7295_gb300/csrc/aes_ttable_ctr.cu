@@ -1,5 +1,5 @@
 // aes_ttable_ctr.cu — instantiates the T-table kernels for Op::kCtr.
-#include "aes_ttable.cuh"
+#include "aes_ttable_launch.cuh"
 
 namespace aesgpu {
 

@@ -1,5 +1,5 @@
 // aes_ttable_dec.cu — instantiates the T-table kernels for Op::kEcbDecrypt.
-#include "aes_ttable.cuh"
+#include "aes_ttable_launch.cuh"
 
 namespace aesgpu {
 

@@ -1,0 +1,71 @@
+// aes_ttable_launch.cuh — host-side launch helpers of the T-table kernels:
+// shape checks, the one-time shared-memory opt-in per device, dispatch over
+// (operation, rounds, blocks per thread).
+#pragma once
+#include "aes_smem_attr.h"
+#include "aes_ttable.cuh"
+
+namespace aesgpu {
+namespace {
+
+template <int NR>
+cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                              const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                              cudaStream_t stream) {
+  auto kern = ttable_ctr_cached_kernel<NR>;
+  cudaError_t e = ensure_dynamic_smem(kern, kTtableSmemEnc);
+  if (e != cudaSuccess) return e;
+  // one warp per run of 256 blocks: no more CTAs than runs / warps per CTA
+  const uint64_t runs = (nblocks + (tail ? 1 : 0) + (cp.ctr0 & 255u) + 255) / 256;
+  const uint64_t warps_per_cta = shape.cta_threads / 32;
+  uint64_t grid = shape.grid_ctas;
+  const uint64_t needed = (runs + warps_per_cta - 1) / warps_per_cta;
+  if (grid > needed) grid = needed > 0 ? needed : 1;
+  kern<<<static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream>>>(
+      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
+  return cudaGetLastError();
+}
+
+template <Op OP, int NR, int BPT>
+cudaError_t launch_one(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                       const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                       cudaStream_t stream) {
+  auto kern = ttable_kernel<OP, NR, BPT>;
+  const int smem = OP == Op::kEcbDecrypt ? kTtableSmemDec : kTtableSmemEnc;
+  cudaError_t e = ensure_dynamic_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<shape.grid_ctas, shape.cta_threads, smem, stream>>>(
+      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
+  return cudaGetLastError();
+}
+
+template <Op OP, int NR>
+cudaError_t dispatch_bpt(const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                         const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                         cudaStream_t stream) {
+  if constexpr (OP == Op::kCtr) {
+    if (shape.blocks_per_thread == 0)  // the run-cached CTR kernel
+      return launch_ctr_cached<NR>(in, out, nblocks, tail, rk, cp, shape, stream);
+  }
+  switch (shape.blocks_per_thread) {
+    case 1: return launch_one<OP, NR, 1>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 2: return launch_one<OP, NR, 2>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 4: return launch_one<OP, NR, 4>(in, out, nblocks, tail, rk, cp, shape, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <Op OP>
+inline cudaError_t dispatch_nr(int nr, const void* in, void* out, uint64_t nblocks, uint32_t tail,
+                        const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
+                        cudaStream_t stream) {
+  switch (nr) {
+    case 10: return dispatch_bpt<OP, 10>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 12: return dispatch_bpt<OP, 12>(in, out, nblocks, tail, rk, cp, shape, stream);
+    case 14: return dispatch_bpt<OP, 14>(in, out, nblocks, tail, rk, cp, shape, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace aesgpu
