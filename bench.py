@@ -328,6 +328,7 @@ def gpu_arm(args):
             result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
         if not args.no_variants:
             result["variants"] = variant_arm(torch, A, args, ks, iv, x, y, value)
+            result["other_modes"] = modes_arm(torch, A, x, y)
         if args.sweep:
             result["sweep"] = sweep(torch, A)
         if args.scaling:
@@ -392,6 +393,22 @@ def read_traffic(args):
     if per_gib is None:
         return None
     return per_gib * (args.size_mib / 1024)
+
+
+def modes_arm(torch, A, x, y):
+    """CBC decryption and XTS (4 KiB units) on the same 1 GiB buffer, AES-128 and AES-256."""
+    out = {}
+    iv = synth.iv_bytes(13)
+    for bits in (128, 256):
+        k1 = A.aes_expand_key(synth.key_bytes(13, bits))
+        k2 = A.aes_expand_key(synth.key_bytes(14, bits))
+        n = x.numel()
+        for name, fn in (("cbc_decrypt", lambda: A.aes_cbc_decrypt(k1, iv, x, y)),
+                         ("xts_encrypt", lambda: A.aes_xts_encrypt(k1, k2, 0, 4096, x, y)),
+                         ("xts_decrypt", lambda: A.aes_xts_decrypt(k1, k2, 0, 4096, x, y))):
+            ms = time_device(torch, fn, 50, 3)
+            out[f"{name}_{bits}_gbps"] = round(n * 50 / (ms / 1e3) / 1e9, 1)
+    return out
 
 
 def variant_arm(torch, A, args, ks, iv, x, y, ttable_gbps):
@@ -516,7 +533,37 @@ def batched_arm(torch, A, ctr128_gbps):
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
         "kernels_per_batch": 4, "graph": True,
     }
-    del b, data
+    # the same messages as ECB + PKCS#7, encrypt then decrypt, against the ECB mix
+    ecb_rates = {}
+    x = synth.bytes_torch(7, synth.STREAM_DATA, 1 << 30, device="cuda")
+    y = torch.empty_like(x)
+    for bits in (128, 192, 256):
+        kse = A.aes_expand_key(synth.key_bytes(7, bits))
+        ms_e = time_device(torch, lambda: A.aes_ecb_encrypt(kse, x, y), 50, 3)
+        ms_d = time_device(torch, lambda: A.aes_ecb_decrypt(kse, x, y), 50, 3)
+        ecb_rates[bits] = ((1 << 30) * 50 / (ms_e / 1e3) / 1e9, (1 << 30) * 50 / (ms_d / 1e3) / 1e9)
+    del x, y
+    del b
+    torch.cuda.empty_cache()
+    enc = B.Batch(B.BATCH_ECB_PKCS7_ENCRYPT, data, in_off, lengths, keys=wl["keys"], key_bits=kb)
+    enc.capture(B.autotune(enc))
+    ms_enc = time_graph(torch, enc, 20)
+    ct_len = (lengths // np.uint64(16) + np.uint64(1)) * np.uint64(16)
+    dec = B.Batch(B.BATCH_ECB_PKCS7_DECRYPT, enc.out, enc.out_off_np, ct_len, keys=wl["keys"], key_bits=kb)
+    dec.capture(B.autotune(dec))
+    ms_dec = time_graph(torch, dec, 20)
+    ok = int((dec.status != 0).sum()) == 0 and bool(torch.equal(dec.out_len.cpu(), torch.from_numpy(lengths.astype(np.int64))))
+    mix_e = sum(by_bits.values()) / sum(by_bits[k] / ecb_rates[k][0] for k in by_bits)
+    mix_d = sum(by_bits.values()) / sum(by_bits[k] / ecb_rates[k][1] for k in by_bits)
+    g_e = nbytes * 20 / (ms_enc / 1e3) / 1e9
+    g_d = float(ct_len.sum()) * 20 / (ms_dec / 1e3) / 1e9
+    out["varlen_16384_ecb_pkcs7"] = {
+        "encrypt_gbps": round(g_e, 1), "decrypt_gbps": round(g_d, 1),
+        "plain_ecb_mix_gbps": {"encrypt": round(mix_e, 1), "decrypt": round(mix_d, 1)},
+        "ratio_vs_plain": {"encrypt": round(g_e / mix_e, 4), "decrypt": round(g_d / mix_d, 4)},
+        "decrypt_restored_every_length": ok,
+    }
+    del enc, dec, data
     torch.cuda.empty_cache()
 
     wl = W.small_messages(4, 1_000_000)

@@ -117,6 +117,33 @@ aes_status aes_ctr_xcrypt_ex(const aes_key_schedule *ks, const uint8_t iv[16], c
                              void *d_out, size_t nbytes, void *stream,
                              const aes_launch_config *cfg);
 
+/* ---- Two more block-parallel modes -------------------------------------
+ * Not in the paper (it names no mode); they reuse the same round kernels. */
+
+/* CBC decryption (SP 800-38A §6.2): block j of d_out is InvCipher(C_j) XOR
+ * C_{j-1}, C_{-1} = iv (host, 16 bytes).  CBC encryption is sequential and
+ * is not offered.  nbytes a multiple of 16 (AES_ERR_LENGTH).  d_in == d_out is
+ * refused (AES_ERR_OVERLAP): each block's predecessor must still be
+ * ciphertext when it is read.  Other pointer rules as aes_ecb_encrypt. */
+aes_status aes_cbc_decrypt(const aes_key_schedule *ks, const uint8_t iv[16], const void *d_in,
+                           void *d_out, size_t nbytes, void *stream);
+
+/* XTS-AES (IEEE 1619 / SP 800-38E) over data units of sector_bytes bytes,
+ * without ciphertext stealing: sector_bytes a positive multiple of 512 and
+ * nbytes a multiple of sector_bytes (AES_ERR_LENGTH).  Unit u (counted from
+ * the start of d_in) uses the tweak value first_sector + u as a 128-bit
+ * little-endian integer: T = Cipher_tweak_ks(value), block j of the unit is
+ * Cipher_data_ks(P ^ T a^j) ^ T a^j with a the generator of GF(2^128) mod
+ * x^128 + x^7 + x^2 + x + 1 (decryption: the inverse cipher in the middle).
+ * data_ks and tweak_ks are the schedules of the two halves of the XTS key.
+ * In place is allowed.  Other pointer rules as aes_ecb_encrypt. */
+aes_status aes_xts_encrypt(const aes_key_schedule *data_ks, const aes_key_schedule *tweak_ks,
+                           uint64_t first_sector, size_t sector_bytes, const void *d_in,
+                           void *d_out, size_t nbytes, void *stream);
+aes_status aes_xts_decrypt(const aes_key_schedule *data_ks, const aes_key_schedule *tweak_ks,
+                           uint64_t first_sector, size_t sector_bytes, const void *d_in,
+                           void *d_out, size_t nbytes, void *stream);
+
 /* ---- Batched messages (one persistent launch) --------------------------
  *
  * Many independent messages of uneven byte lengths, each with its own key

@@ -325,6 +325,88 @@ int ref_ecb_pkcs7_decrypt(const uint8_t *key, int key_bits, const uint8_t *in, u
     return REF_OK;
 }
 
+/* ---- CBC, SP 800-38A §6.2 ---------------------------------------------- */
+
+int ref_cbc_encrypt(const uint8_t *key, int key_bits, const uint8_t iv[16], const uint8_t *in,
+                    uint8_t *out, uint64_t n) {
+    uint8_t w[240], chain[16], x[16];
+    int nr;
+    if (ref_key_expansion(key, key_bits, w, &nr) < 0) return REF_ERR_KEYSIZE;
+    if (n % 16) return REF_ERR_LENGTH;
+    memcpy(chain, iv, 16);
+    for (uint64_t off = 0; off < n; off += 16) {
+        for (int b = 0; b < 16; ++b) x[b] = (uint8_t)(in[off + b] ^ chain[b]);
+        ref_cipher(x, out + off, w, nr);
+        memcpy(chain, out + off, 16);
+    }
+    return REF_OK;
+}
+
+int ref_cbc_decrypt(const uint8_t *key, int key_bits, const uint8_t iv[16], const uint8_t *in,
+                    uint8_t *out, uint64_t n) {
+    uint8_t w[240], prev[16], cur[16], x[16];
+    int nr;
+    if (ref_key_expansion(key, key_bits, w, &nr) < 0) return REF_ERR_KEYSIZE;
+    if (n % 16) return REF_ERR_LENGTH;
+    memcpy(prev, iv, 16);
+    for (uint64_t off = 0; off < n; off += 16) {
+        memcpy(cur, in + off, 16); /* kept before `out` may overwrite it in place */
+        ref_inv_cipher(cur, x, w, nr);
+        for (int b = 0; b < 16; ++b) out[off + b] = (uint8_t)(x[b] ^ prev[b]);
+        memcpy(prev, cur, 16);
+    }
+    return REF_OK;
+}
+
+/* ---- XTS, IEEE 1619 (no ciphertext stealing) --------------------------- */
+
+/* T * alpha: the 16 bytes as a little-endian 128-bit integer shifted left by
+ * one, the bit shifted out of byte 15 folded back as 0x87 into byte 0. */
+static void xts_double(uint8_t t[16]) {
+    unsigned carry = 0;
+    for (int i = 0; i < 16; ++i) {
+        unsigned v = ((unsigned)t[i] << 1) | carry;
+        carry = (t[i] >> 7) & 1u;
+        t[i] = (uint8_t)v;
+    }
+    if (carry) t[0] ^= 0x87u;
+}
+
+static int xts_run(int decrypt, const uint8_t *key1, const uint8_t *key2, int key_bits,
+                   uint64_t sector_bytes, uint64_t first_sector, const uint8_t *in, uint8_t *out,
+                   uint64_t n) {
+    uint8_t w1[240], w2[240], t[16], x[16], y[16];
+    int nr1, nr2;
+    if (ref_key_expansion(key1, key_bits, w1, &nr1) < 0) return REF_ERR_KEYSIZE;
+    if (ref_key_expansion(key2, key_bits, w2, &nr2) < 0) return REF_ERR_KEYSIZE;
+    if (sector_bytes == 0 || sector_bytes % 16 || n % sector_bytes) return REF_ERR_LENGTH;
+    for (uint64_t u = 0; u < n / sector_bytes; ++u) {
+        uint64_t sector = first_sector + u;
+        uint8_t tv[16] = {0};
+        for (int i = 0; i < 8; ++i) tv[i] = (uint8_t)(sector >> (8 * i));
+        ref_cipher(tv, t, w2, nr2); /* T = CIPH_K2(tweak value) */
+        for (uint64_t j = 0; j < sector_bytes / 16; ++j) {
+            const uint64_t off = u * sector_bytes + 16 * j;
+            for (int b = 0; b < 16; ++b) x[b] = (uint8_t)(in[off + b] ^ t[b]);
+            if (decrypt) ref_inv_cipher(x, y, w1, nr1);
+            else ref_cipher(x, y, w1, nr1);
+            for (int b = 0; b < 16; ++b) out[off + b] = (uint8_t)(y[b] ^ t[b]);
+            xts_double(t);
+        }
+    }
+    return REF_OK;
+}
+
+int ref_xts_encrypt(const uint8_t *key1, const uint8_t *key2, int key_bits, uint64_t sector_bytes,
+                    uint64_t first_sector, const uint8_t *in, uint8_t *out, uint64_t n) {
+    return xts_run(0, key1, key2, key_bits, sector_bytes, first_sector, in, out, n);
+}
+
+int ref_xts_decrypt(const uint8_t *key1, const uint8_t *key2, int key_bits, uint64_t sector_bytes,
+                    uint64_t first_sector, const uint8_t *in, uint8_t *out, uint64_t n) {
+    return xts_run(1, key1, key2, key_bits, sector_bytes, first_sector, in, out, n);
+}
+
 /* ---- The paper's pthreads scheme, §IV.B -------------------------------- */
 
 typedef struct {

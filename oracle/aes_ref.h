@@ -78,6 +78,25 @@ int ref_ecb_pkcs7_encrypt(const uint8_t *key, int key_bits, const uint8_t *in, u
 int ref_ecb_pkcs7_decrypt(const uint8_t *key, int key_bits, const uint8_t *in, uint64_t n,
                           uint8_t *out, uint64_t *out_len);
 
+/* CBC (SP 800-38A §6.2): C_j = CIPH(P_j ^ C_{j-1}), C_0 = IV; n a multiple
+ * of 16.  Decryption P_j = CIPH^-1(C_j) ^ C_{j-1}.  in == out allowed. */
+int ref_cbc_encrypt(const uint8_t *key, int key_bits, const uint8_t iv[16], const uint8_t *in,
+                    uint8_t *out, uint64_t n);
+int ref_cbc_decrypt(const uint8_t *key, int key_bits, const uint8_t iv[16], const uint8_t *in,
+                    uint8_t *out, uint64_t n);
+
+/* XTS-AES (IEEE 1619 / SP 800-38E) without ciphertext stealing: the buffer
+ * is n / sector_bytes data units (n a multiple of sector_bytes, sector_bytes
+ * a positive multiple of 16); unit u has the tweak value first_sector + u as a
+ * 128-bit little-endian integer; T = CIPH_K2(tweak), then for each block
+ * C = CIPH_K1(P ^ T) ^ T and T = T * alpha in GF(2^128) (shift left by one
+ * bit of the little-endian value, 0x87 folded into byte 0 on carry out).
+ * key1 encrypts the data, key2 the tweak; both key_bits. */
+int ref_xts_encrypt(const uint8_t *key1, const uint8_t *key2, int key_bits, uint64_t sector_bytes,
+                    uint64_t first_sector, const uint8_t *in, uint8_t *out, uint64_t n);
+int ref_xts_decrypt(const uint8_t *key1, const uint8_t *key2, int key_bits, uint64_t sector_bytes,
+                    uint64_t first_sector, const uint8_t *in, uint8_t *out, uint64_t n);
+
 /* The paper's pthreads scheme (§IV.B): nthreads contiguous chunks of whole
  * blocks, the remainder (and any partial CTR block) in the last chunk, one
  * thread per chunk running the single-threaded routine, joined.  nthreads < 1

@@ -76,6 +76,13 @@ def _declare(lib):
     lib.ref_ctr_xcrypt_mt.restype = ctypes.c_int
     lib.ref_ctr_xcrypt_blocks.argtypes = [u8p, ctypes.c_int, u8p, u8p, u8p, u8p, ctypes.c_uint64]
     lib.ref_ctr_xcrypt_blocks.restype = ctypes.c_int
+    for name in ("ref_cbc_encrypt", "ref_cbc_decrypt"):
+        getattr(lib, name).argtypes = [u8p, ctypes.c_int, u8p, u8p, u8p, ctypes.c_uint64]
+        getattr(lib, name).restype = ctypes.c_int
+    for name in ("ref_xts_encrypt", "ref_xts_decrypt"):
+        getattr(lib, name).argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, u8p, u8p,
+                                       ctypes.c_uint64]
+        getattr(lib, name).restype = ctypes.c_int
     lib.ref_pkcs7_padded_len.argtypes = [ctypes.c_uint64]
     lib.ref_pkcs7_padded_len.restype = ctypes.c_uint64
     for name in ("ref_ecb_pkcs7_encrypt", "ref_ecb_pkcs7_decrypt"):
@@ -237,3 +244,23 @@ class Oracle:
         if rc != REF_OK:
             return rc, None
         return rc, out[: n.value].copy()
+
+    def cbc_encrypt(self, key, key_bits: int, iv, data) -> np.ndarray:
+        k, v, d = _u8(key), _u8(iv), _u8(data)
+        out = np.empty_like(d)
+        _check(self.lib.ref_cbc_encrypt(_ptr(k), key_bits, _ptr(v), _ptr(d), _ptr(out), d.size), "cbc_encrypt")
+        return out
+
+    def cbc_decrypt(self, key, key_bits: int, iv, data) -> np.ndarray:
+        k, v, d = _u8(key), _u8(iv), _u8(data)
+        out = np.empty_like(d)
+        _check(self.lib.ref_cbc_decrypt(_ptr(k), key_bits, _ptr(v), _ptr(d), _ptr(out), d.size), "cbc_decrypt")
+        return out
+
+    def xts(self, decrypt: bool, key1, key2, key_bits: int, sector_bytes: int, first_sector: int,
+            data) -> np.ndarray:
+        k1, k2, d = _u8(key1), _u8(key2), _u8(data)
+        out = np.empty_like(d)
+        fn = self.lib.ref_xts_decrypt if decrypt else self.lib.ref_xts_encrypt
+        _check(fn(_ptr(k1), _ptr(k2), key_bits, sector_bytes, first_sector, _ptr(d), _ptr(out), d.size), "xts")
+        return out

@@ -12,8 +12,11 @@ from .aes import (  # noqa: F401
     VARIANT_AUTO,
     VARIANT_BITSLICE,
     VARIANT_TTABLE,
+    aes_cbc_decrypt,
     aes_ctr_xcrypt,
     aes_ecb_decrypt,
     aes_ecb_encrypt,
     aes_expand_key,
+    aes_xts_decrypt,
+    aes_xts_encrypt,
 )

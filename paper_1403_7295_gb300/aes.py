@@ -69,6 +69,11 @@ def lib():
             getattr(L, name + "_ex").argtypes = [ksp, vp, vp, sz, vp, cfgp]
         L.aes_ctr_xcrypt.argtypes = [ksp, vp, vp, vp, sz, vp]
         L.aes_ctr_xcrypt_ex.argtypes = [ksp, vp, vp, vp, sz, vp, cfgp]
+        L.aes_cbc_decrypt.argtypes = [ksp, vp, vp, vp, sz, vp]
+        for name in ("aes_xts_encrypt", "aes_xts_decrypt"):
+            getattr(L, name).argtypes = [ksp, ksp, ctypes.c_uint64, sz, vp, vp, sz, vp]
+            getattr(L, name).restype = ctypes.c_int
+        L.aes_cbc_decrypt.restype = ctypes.c_int
         L.aes_last_cuda_error.argtypes = []
         L.aes_status_string.argtypes = [ctypes.c_int]
         L.aes_status_string.restype = ctypes.c_char_p
@@ -162,4 +167,36 @@ def aes_ctr_xcrypt(ks: KeySchedule, iv, inp, out=None, stream=None, config=None)
     _check(lib().aes_ctr_xcrypt_ex(ctypes.byref(ks), ctypes.cast(vb, ctypes.c_void_p), inp.data_ptr(),
                                    out.data_ptr(), inp.numel(), _stream_handle(stream, inp),
                                    _cfg(config)), "aes_ctr_xcrypt")
+    return out
+
+
+def aes_cbc_decrypt(ks: KeySchedule, iv, inp, out=None, stream=None):
+    """CBC decryption of a device uint8 tensor (not in place); returns ``out``."""
+    inp, out = _prepare(inp, out)
+    v = _host_bytes(iv)
+    if v.size != 16:
+        raise ValueError("iv must be 16 bytes")
+    vb = (ctypes.c_uint8 * 16).from_buffer_copy(v.tobytes())
+    _check(lib().aes_cbc_decrypt(ctypes.byref(ks), ctypes.cast(vb, ctypes.c_void_p), inp.data_ptr(),
+                                 out.data_ptr(), inp.numel(), _stream_handle(stream, inp)), "aes_cbc_decrypt")
+    return out
+
+
+def aes_xts_encrypt(data_ks: KeySchedule, tweak_ks: KeySchedule, first_sector: int, sector_bytes: int,
+                    inp, out=None, stream=None):
+    """XTS encryption of a device uint8 tensor of whole data units; returns ``out``."""
+    inp, out = _prepare(inp, out)
+    _check(lib().aes_xts_encrypt(ctypes.byref(data_ks), ctypes.byref(tweak_ks), first_sector, sector_bytes,
+                                 inp.data_ptr(), out.data_ptr(), inp.numel(), _stream_handle(stream, inp)),
+           "aes_xts_encrypt")
+    return out
+
+
+def aes_xts_decrypt(data_ks: KeySchedule, tweak_ks: KeySchedule, first_sector: int, sector_bytes: int,
+                    inp, out=None, stream=None):
+    """XTS decryption of a device uint8 tensor of whole data units; returns ``out``."""
+    inp, out = _prepare(inp, out)
+    _check(lib().aes_xts_decrypt(ctypes.byref(data_ks), ctypes.byref(tweak_ks), first_sector, sector_bytes,
+                                 inp.data_ptr(), out.data_ptr(), inp.numel(), _stream_handle(stream, inp)),
+           "aes_xts_decrypt")
     return out

@@ -216,6 +216,55 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
   return AES_OK;
 }
 
+// CBC decryption and XTS: validation shared with the other single-buffer calls.
+aes_status run_cbc_decrypt(const aes_key_schedule* ks, const uint8_t* iv, const void* in, void* out,
+                           size_t nbytes, void* stream) {
+  aes_status s = check_schedule(ks);
+  if (s != AES_OK) return s;
+  if (iv == nullptr) return AES_ERR_ARG;
+  if (nbytes % 16 != 0) return AES_ERR_LENGTH;
+  if (nbytes == 0) return AES_OK;
+  if (in == out && in != nullptr) return AES_ERR_OVERLAP;  // a predecessor must still be ciphertext
+  const void* din = nullptr;
+  void* dout = nullptr;
+  s = check_buffers(in, out, nbytes, &din, &dout);
+  if (s != AES_OK) return s;
+  RoundKeys rk;
+  copy_round_keys(ks->rk_dec, static_cast<int>(ks->nr), &rk);
+  CtrParams cp{};
+  for (int c = 0; c < 4; ++c) cp.iv_w[c] = load_le32(iv + 4 * c);
+  const LaunchShape shape{1024, 1, sm_count()};
+  const cudaError_t e = launch_cbc_decrypt(static_cast<int>(ks->nr), din, dout, nbytes / 16, rk, cp, shape,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? AES_OK : cuda_failure(e);
+}
+
+aes_status run_xts(bool decrypt, const aes_key_schedule* data_ks, const aes_key_schedule* tweak_ks,
+                   uint64_t first_sector, size_t sector_bytes, const void* in, void* out, size_t nbytes,
+                   void* stream) {
+  aes_status s = check_schedule(data_ks);
+  if (s != AES_OK) return s;
+  s = check_schedule(tweak_ks);
+  if (s != AES_OK) return s;
+  if (sector_bytes == 0 || sector_bytes % 512 != 0 || sector_bytes / 16 > 0xFFFFFFFFull ||
+      nbytes % sector_bytes != 0)
+    return AES_ERR_LENGTH;
+  if (nbytes == 0) return AES_OK;
+  const void* din = nullptr;
+  void* dout = nullptr;
+  s = check_buffers(in, out, nbytes, &din, &dout);
+  if (s != AES_OK) return s;
+  RoundKeys rk1, rk2;
+  copy_round_keys(decrypt ? data_ks->rk_dec : data_ks->rk_enc, static_cast<int>(data_ks->nr), &rk1);
+  copy_round_keys(tweak_ks->rk_enc, static_cast<int>(tweak_ks->nr), &rk2);
+  const LaunchShape shape{1024, 1, sm_count()};
+  const cudaError_t e = launch_xts_mode(decrypt, static_cast<int>(data_ks->nr), static_cast<int>(tweak_ks->nr),
+                                        din, dout, nbytes / 16, rk1, rk2, first_sector,
+                                        static_cast<uint32_t>(sector_bytes / 16), shape,
+                                        static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? AES_OK : cuda_failure(e);
+}
+
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* stream,
@@ -348,6 +397,23 @@ aes_status aes_ecb_decrypt(const aes_key_schedule* ks, const void* d_in, void* d
 aes_status aes_ctr_xcrypt(const aes_key_schedule* ks, const uint8_t iv[16], const void* d_in,
                           void* d_out, size_t nbytes, void* stream) {
   return aes_ctr_xcrypt_ex(ks, iv, d_in, d_out, nbytes, stream, nullptr);
+}
+
+aes_status aes_cbc_decrypt(const aes_key_schedule* ks, const uint8_t iv[16], const void* d_in, void* d_out,
+                           size_t nbytes, void* stream) {
+  return run_cbc_decrypt(ks, iv, d_in, d_out, nbytes, stream);
+}
+
+aes_status aes_xts_encrypt(const aes_key_schedule* data_ks, const aes_key_schedule* tweak_ks,
+                           uint64_t first_sector, size_t sector_bytes, const void* d_in, void* d_out,
+                           size_t nbytes, void* stream) {
+  return run_xts(false, data_ks, tweak_ks, first_sector, sector_bytes, d_in, d_out, nbytes, stream);
+}
+
+aes_status aes_xts_decrypt(const aes_key_schedule* data_ks, const aes_key_schedule* tweak_ks,
+                           uint64_t first_sector, size_t sector_bytes, const void* d_in, void* d_out,
+                           size_t nbytes, void* stream) {
+  return run_xts(true, data_ks, tweak_ks, first_sector, sector_bytes, d_in, d_out, nbytes, stream);
 }
 
 size_t aes_batch_workspace_size(uint32_t n_msgs) { return batch_workspace_bytes(n_msgs); }

@@ -50,6 +50,16 @@ cudaError_t launch_bitslice(Op op, int nr, const void* in, void* out, uint64_t n
 constexpr int kBitsliceThreads = 128;
 constexpr int kBitsliceBlocksPerCta = 4 * 512;  // 4 warps x 512 blocks per iteration
 
+// CBC decryption (rk: the equivalent inverse schedule; cp.iv_w: the IV) and
+// XTS (rk1: data key, encryption or equivalent inverse schedule; rk2: tweak
+// key, encryption schedule; nblocks a multiple of 32, sector_blocks too).
+cudaError_t launch_cbc_decrypt(int nr, const void* in, void* out, uint64_t nblocks, const RoundKeys& rk,
+                               const CtrParams& cp, const LaunchShape& shape, cudaStream_t stream);
+cudaError_t launch_xts_mode(bool decrypt, int nr, int nr_tweak, const void* in, void* out,
+                            uint64_t nblocks, const RoundKeys& rk1, const RoundKeys& rk2,
+                            uint64_t first_sector, uint32_t sector_blocks, const LaunchShape& shape,
+                            cudaStream_t stream);
+
 // Dynamic shared memory of the T-table kernels (bytes).
 constexpr int kTtableSmemEnc = 128 * 1024;
 constexpr int kTtableSmemDec = 192 * 1024;

@@ -120,3 +120,20 @@ def test_status_strings(lib):
     for s in range(11):
         assert lib.aes_status_string(s)
     assert lib.aes_status_string(99) == b"unknown status"
+
+
+def test_cbc_and_xts_validation(lib):
+    ks = A.aes_expand_key(synth.key_bytes(0, 128))
+    kr = ctypes.byref(ks)
+    ivb = (ctypes.c_uint8 * 16)()
+    base = 1 << 20
+    assert lib.aes_cbc_decrypt(kr, ivb, base, base, 64, None) == 5           # in place refused
+    assert lib.aes_cbc_decrypt(kr, ivb, base, base + 4096, 17, None) == 3    # whole blocks only
+    assert lib.aes_cbc_decrypt(kr, None, base, base + 4096, 16, None) == 1   # IV required
+    assert lib.aes_cbc_decrypt(kr, ivb, base, base + 4096, 0, None) == 0
+    for fn in (lib.aes_xts_encrypt, lib.aes_xts_decrypt):
+        assert fn(kr, kr, 0, 496, base, base, 496, None) == 3                # unit not a multiple of 512
+        assert fn(kr, kr, 0, 512, base, base, 1000, None) == 3               # not whole units
+        assert fn(kr, None, 0, 512, base, base, 512, None) == 1
+        assert fn(kr, kr, 0, 512, base + 8, base + 8, 512, None) == 4        # misaligned
+        assert fn(kr, kr, 0, 512, base, base, 0, None) == 0

@@ -240,6 +240,60 @@ def test_ctr_first_block_and_sampled_blocks(oracle):
 
 
 # ---------------------------------------------------------------------------
+# CBC and XTS
+# ---------------------------------------------------------------------------
+
+def openssl_cbc(key, iv, data, decrypt=False):
+    c = _openssl()
+    ctx = c.Cipher(c.algorithms.AES(bytes(key)), c.modes.CBC(bytes(iv)))
+    op = ctx.decryptor() if decrypt else ctx.encryptor()
+    return np.frombuffer(op.update(bytes(data)) + op.finalize(), np.uint8)
+
+
+def openssl_xts(key1, key2, sector_bytes, first_sector, data, decrypt=False):
+    c = _openssl()
+    out = []
+    for u in range(len(data) // sector_bytes):
+        tweak = (first_sector + u).to_bytes(16, "little")
+        ctx = c.Cipher(c.algorithms.AES(bytes(key1) + bytes(key2)), c.modes.XTS(tweak))
+        op = ctx.decryptor() if decrypt else ctx.encryptor()
+        out.append(op.update(bytes(data[u * sector_bytes:(u + 1) * sector_bytes])) + op.finalize())
+    return np.frombuffer(b"".join(out), np.uint8)
+
+
+@pytest.mark.parametrize("bits", KEY_BITS)
+def test_cbc_matches_openssl_and_ecb(oracle, bits):
+    key = synth.key_bytes(61, bits)
+    iv = synth.bytes_np(61, synth.STREAM_NONCE, 16)
+    data = synth.bytes_np(61, synth.STREAM_DATA, 16 * 333)
+    ct = oracle.cbc_encrypt(key, bits, iv, data)
+    assert np.array_equal(ct, openssl_cbc(key, iv, data))
+    assert np.array_equal(oracle.cbc_decrypt(key, bits, iv, ct), data)
+    # P_j = InvCipher(C_j) ^ C_{j-1}: CBC decryption is ECB decryption XOR the shifted ciphertext
+    chain = np.concatenate([iv, ct[:-16]])
+    assert np.array_equal(oracle.ecb_decrypt(key, bits, ct) ^ chain, data)
+
+
+@pytest.mark.parametrize("bits", (128, 256))
+@pytest.mark.parametrize("sector_bytes,first_sector", [(16, 0), (512, 7), (4096, (1 << 40) + 3)])
+def test_xts_matches_openssl(oracle, bits, sector_bytes, first_sector):
+    key1 = synth.key_bytes(62, bits)
+    key2 = synth.key_bytes(63, bits)
+    data = synth.bytes_np(62, synth.STREAM_DATA, 3 * sector_bytes)
+    ct = oracle.xts(False, key1, key2, bits, sector_bytes, first_sector, data)
+    assert np.array_equal(ct, openssl_xts(key1, key2, sector_bytes, first_sector, data))
+    assert np.array_equal(oracle.xts(True, key1, key2, bits, sector_bytes, first_sector, ct), data)
+
+
+def test_xts_rejects_bad_lengths(oracle):
+    k = np.zeros(16, np.uint8)
+    with pytest.raises(ValueError):
+        oracle.xts(False, k, k, 128, 512, 0, np.zeros(513, np.uint8))
+    with pytest.raises(ValueError):
+        oracle.xts(False, k, k, 128, 24, 0, np.zeros(48, np.uint8))
+
+
+# ---------------------------------------------------------------------------
 # PKCS#7
 # ---------------------------------------------------------------------------
 
@@ -324,6 +378,9 @@ MUTANTS = {
     "inv_mix_coef": ("{14, 11, 13, 9}, {9, 14, 11, 13}", "{14, 11, 13, 9}, {9, 14, 13, 11}"),
     "pkcs7_check": ("if (out[k] != p) return REF_ERR_PADDING;", "if (out[k] != p) break;"),
     "chunk_offset": ("first_block + b0, in + 16 * b0", "first_block, in + 16 * b0"),
+    "cbc_chain": ("        memcpy(prev, cur, 16);", "        memcpy(prev, out + off, 16);"),
+    "xts_poly": ("if (carry) t[0] ^= 0x87u;", "if (carry) t[0] ^= 0x86u;"),
+    "xts_tweak_order": ("tv[i] = (uint8_t)(sector >> (8 * i));", "tv[15 - i] = (uint8_t)(sector >> (8 * i));"),
 }
 
 
@@ -361,6 +418,13 @@ def battery(o: Oracle) -> list:
                                             o.ctr_xcrypt(key, 128, iv, big)))
     bad = openssl_ecb(key, np.frombuffer(b"B" * 16 + bytes(14) + b"\x02\x03", np.uint8))
     check("pkcs7_reject", lambda: o.ecb_pkcs7_decrypt(key, 128, bad)[0] != 0)
+    civ = synth.bytes_np(45, synth.STREAM_NONCE, 16)
+    cdat = synth.bytes_np(45, synth.STREAM_DATA, 16 * 6)
+    check("cbc", lambda: np.array_equal(o.cbc_decrypt(key, 128, civ, openssl_cbc(key, civ, cdat)), cdat))
+    k2 = synth.key_bytes(46, 128)
+    xdat = synth.bytes_np(46, synth.STREAM_DATA, 16 * 24)
+    check("xts", lambda: np.array_equal(o.xts(False, key, k2, 128, 16 * 12, 5, xdat),
+                                        openssl_xts(key, k2, 16 * 12, 5, xdat)))
     return fails
 
 
