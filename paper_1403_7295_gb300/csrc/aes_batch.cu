@@ -490,6 +490,63 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
   }
 }
 
+// A whole span (256 blocks) inside one message, every block whole: the same
+// work as process_block with the round count fixed and no per-block checks.
+template <int OPB, int NR>
+__device__ __forceinline__ void span_fast(const BatchArgs& a, const Tabs& T, const Slot* slots,
+                                          const uint32_t* rk, const Cur& c, uint32_t span,
+                                          uint32_t lane, RunCache& rc) {
+  const uint4* src = reinterpret_cast<const uint4*>(c.src) + span + lane;
+  uint4* dst = reinterpret_cast<uint4*>(c.dst) + span + lane;
+  uint4 v = __ldcs(src);
+#pragma unroll 1
+  for (uint32_t k = 0; k < 8; ++k) {
+    uint4 vn = v;
+    if (k < 7) vn = __ldcs(src + 32 * (k + 1));
+    State s;
+    if (OPB == kBatchCtr) {
+      const uint32_t ctr = c.ctr + span + 32 * k + lane;
+      if ((ctr >> 8) != rc.run || c.slot + 1 != rc.slot) {
+        rc.run = ctr >> 8;
+        rc.slot = c.slot + 1;
+        rc.xr = __byte_perm(ctr & ~255u, 0, 0x0123) ^ rk[kCtrRk0w3];
+        const uint4 c1 = lds128(rk + kCtrC1);
+        rc.c10 = c1.x;
+        const uint32_t s1 = c1.y ^ T.t2(rc.xr), s2 = c1.z ^ T.t1(rc.xr), s3 = c1.w ^ T.t0(rc.xr);
+        const uint4 k2 = lds128(rk + 8);
+        rc.d0 = k2.x ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
+        rc.d1 = k2.y ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
+        rc.d2 = k2.z ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
+        rc.d3 = k2.w ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
+      }
+      const uint32_t s0 = rc.c10 ^ T.t3(rc.xr ^ ((ctr & 255u) << 24));
+      s = State{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
+      s = enc_rounds_smem<NR>(T, s, rk, 3);
+      __stcs(dst + 32 * k, make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3));
+    } else if (OPB == kBatchEcbEnc) {
+      const uint4 k0 = lds128(rk);
+      s = State{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+      s = enc_rounds_smem<NR>(T, s, rk, 1);
+      __stcs(dst + 32 * k, make_uint4(s.s0, s.s1, s.s2, s.s3));
+    } else {
+      const uint4 k0 = lds128(rk);
+      s = State{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+      s = dec_rounds_smem<NR>(T, s, rk);
+      __stcs(dst + 32 * k, make_uint4(s.s0, s.s1, s.s2, s.s3));
+      const uint32_t gr = span + 32 * k + lane;
+      if (((c.nr >> 16) & 1u) && gr + 1 == c.e) {  // the message's last block: check PKCS#7
+        const Slot& sl = slots[c.slot];
+        const uint32_t p = state_byte(s, 15);
+        bool ok = p >= 1 && p <= 16;
+        for (uint32_t q = 16 - (ok ? p : 0); q < 16; ++q) ok = ok && state_byte(s, q) == p;
+        if (a.status) a.status[sl.msg] = ok ? AES_OK : AES_ERR_PADDING;
+        if (a.out_len) a.out_len[sl.msg] = ok ? 16 * (sl.blk_end - sl.blk_start) - p : 0;
+      }
+    }
+    v = vn;
+  }
+}
+
 // Warp 0: claim the next tile and find its first and last message.
 __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total,
                                            unsigned long long* s_tile, uint32_t* s_mlo,
@@ -578,6 +635,22 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
         const uint32_t span = gr0 + sp * 256;
         if (span >= gr1) break;
         have_next = false;
+        if (span + 256 <= gr1) {
+          // every lane takes the message of the span's first block; if that
+          // message holds the whole span in whole blocks, run the fast loop
+          if (span < c.s || span >= c.e) select_message(slots, wn, t0, t1, span, c);
+          const bool whole = span >= c.s && span + 256 <= c.f &&
+                             (OPB != kBatchCtr || ((c.nr >> 17) & 1u));
+          if (whole) {
+            const uint32_t* rk = rk_all + c.slot * kRkStride;
+            switch (c.nr & 0xFFu) {
+              case 10: span_fast<OPB, 10>(a, T, slots, rk, c, span, lane, rc); break;
+              case 12: span_fast<OPB, 12>(a, T, slots, rk, c, span, lane, rc); break;
+              default: span_fast<OPB, 14>(a, T, slots, rk, c, span, lane, rc); break;
+            }
+            continue;
+          }
+        }
         for (uint32_t k = 0; k < 8; ++k) {
           const uint32_t gr = span + 32 * k + lane;
           if (gr >= gr1) break;
