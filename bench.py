@@ -64,8 +64,9 @@ def parse_args():
     p.add_argument("--no-probes", action="store_true")
     p.add_argument("--no-variants", action="store_true", help="skip the T-table vs bitsliced comparison")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-message workloads")
-    p.add_argument("--only", choices=["all", "batched"], default="all",
-                   help="'batched': time only the batched varlen workload (for profiling)")
+    p.add_argument("--only", choices=["all", "batched", "small"], default="all",
+                   help="'batched': time only the batched varlen workload; 'small': only the "
+                        "1,000,000 packet-sized messages (profiling entries)")
     p.add_argument("--batch-msgs", type=int, default=16384, help="messages in the batched varlen workload")
     p.add_argument("--serve-seconds", type=float, default=10.0,
                    help="duration of the serving leg (Poisson 50k req/s); 0 skips it")
@@ -216,7 +217,7 @@ def time_device(torch, fn, steps, warmup, barrier=None):
 def gpu_arm(args):
     import torch
 
-    if args.only == "batched":
+    if args.only in ("batched", "small"):
         return batched_only(args)
 
     from paper_1403_7295_gb300 import aes as A
@@ -464,8 +465,10 @@ def time_graph(torch, b, steps):
 
 
 def batched_only(args):
-    """Just the batched varlen CTR workload at --batch-msgs messages: --warmup
-    then --steps graph replays (the profiling entry for the batch kernel)."""
+    """Just one batched CTR workload: the varlen one at --batch-msgs messages
+    (tile 32768), or with --only small the 1,000,000 packet-sized AES-128
+    messages (tile 8192); --warmup then --steps graph replays (the profiling
+    entries for the batch kernel)."""
     import torch
 
     from paper_1403_7295_gb300 import aes as A
@@ -475,15 +478,17 @@ def batched_only(args):
 
     BLD.build()
     A.lib()
-    wl = W.batched_varlen(3, args.batch_msgs)
+    small = args.only == "small"
+    wl = W.small_messages(4, 1_000_000) if small else W.batched_varlen(3, args.batch_msgs)
     lengths = wl["lengths"]
     in_off, total = B.pack_offsets(lengths)
     data = synth.bytes_torch(3, synth.STREAM_DATA, total, device="cuda")
     b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=wl["key_bits"], ivs=wl["ivs"])
-    b.capture(B.AesBatchConfig(1024, 32768, 0, 0))
+    b.capture(B.AesBatchConfig(1024, 8192 if small else 32768, 0, 0))
     ms = time_graph(torch, b, args.steps) if args.warmup >= 3 else time_device(torch, b.replay, args.steps, args.warmup)
     gbps = b.total_input_bytes() * args.steps / (ms / 1e3) / 1e9
-    print(json.dumps({"workload": f"batched varlen CTR, {args.batch_msgs} messages", "bytes": b.total_input_bytes(),
+    name = "1,000,000 packet-sized messages" if small else f"{args.batch_msgs} messages"
+    print(json.dumps({"workload": f"batched varlen CTR, {name}", "bytes": b.total_input_bytes(),
                       "gbps": round(gbps, 1), "ms_per_batch": round(ms / args.steps, 3)}), flush=True)
 
 

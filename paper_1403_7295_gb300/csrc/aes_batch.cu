@@ -347,7 +347,11 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
     const uint32_t nr = ks.nr;
     sl.nr = nr;
     const uint32_t* src = OPB == kBatchEcbDec ? ks.rk_dec : ks.rk_enc;
-    for (uint32_t i = 0; i < 4 * (nr + 1); ++i) rk[i] = src[i];
+    const uint32_t nw = 4 * (nr + 1);
+    // read-only loads, independent of the shared-memory stores: all in flight together
+#pragma unroll
+    for (uint32_t i = 0; i < 60; ++i)
+      if (i < nw) rk[i] = __ldg(src + i);
   }
   if (OPB == kBatchCtr) {
     const uint4 ivw = *reinterpret_cast<const uint4*>(a.iv + 16ull * m);
@@ -381,10 +385,19 @@ struct Cur {
   uint64_t src, dst;  // byte address of tile block 0 in this message's input / output
 };
 
+// The message of tile block gr.  A thread's blocks only move forward through
+// a window, so the search starts at its current slot and steps forward a few
+// slots (short messages: usually one step) before falling back to a binary
+// search over the rest of the window.
 __device__ __forceinline__ void select_message(const Slot* slots, uint32_t wn, uint64_t t0,
                                                uint64_t t1, uint32_t gr, Cur& c) {
   const uint64_t g = t0 + gr;
-  uint32_t lo = 0, hi = wn;  // last slot whose first block is <= g
+  uint32_t lo = c.slot, hi = wn;  // last slot whose first block is <= g, in [lo, hi)
+#pragma unroll 1
+  for (int i = 0; i < 3 && lo + 1 < hi; ++i) {
+    if (slots[lo + 1].blk_start > g) hi = lo + 1;
+    else ++lo;
+  }
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
     if (slots[mid].blk_start <= g) lo = mid;
@@ -405,6 +418,47 @@ __device__ __forceinline__ void select_message(const Slot* slots, uint32_t wn, u
   c.dst = sl.dst0 + 16 * t0;
 }
 
+// Bytes [0, n) of a 16-byte-aligned block, zero above (n < 16): whole words
+// first, then the bytes of the last word.  Every load is independent of the
+// others, so they are in flight together.
+__device__ __forceinline__ uint4 load_partial(const uint8_t* p, uint32_t n) {
+  uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    if (4 * q + 4 <= n) {
+      w[q] = __ldcs(reinterpret_cast<const unsigned int*>(p + 4 * q));
+    } else {
+#pragma unroll
+      for (uint32_t b = 0; b < 3; ++b)
+        if (4 * q + b < n) w[q] |= static_cast<uint32_t>(__ldcs(p + 4 * q + b)) << (8 * b);
+    }
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Store bytes [0, n) of v at a 16-byte-aligned address (n < 16).
+__device__ __forceinline__ void store_partial(uint8_t* p, const uint4& v, uint32_t n) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (uint32_t q = 0; q < 4; ++q) {
+    if (4 * q + 4 <= n) {
+      __stcs(reinterpret_cast<unsigned int*>(p + 4 * q), w[q]);
+    } else {
+#pragma unroll
+      for (uint32_t b = 0; b < 3; ++b)
+        if (4 * q + b < n) p[4 * q + b] = static_cast<uint8_t>(w[q] >> (8 * b));
+    }
+  }
+}
+
+// Input of tile block gr of the current message: a whole block, or the
+// leading `rem` bytes of the last one (zero above).
+template <int OPB>
+__device__ __forceinline__ uint4 load_block(const Cur& c, uint32_t gr) {
+  if (OPB == kBatchEcbDec || gr < c.f) return __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
+  return load_partial(reinterpret_cast<const uint8_t*>(c.src + 16ull * gr), (c.nr >> 8) & 0xFFu);
+}
+
 // Per-thread cache of one CTR counter run (256 aligned counters of one
 // message): after round 1 only column 0 depends on the counter's low byte,
 // so round 2 is d_j ^ (one lookup) for the whole run.
@@ -420,7 +474,6 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
                                               const uint4& v_in, RunCache& rc) {
   const uint32_t nr = c.nr & 0xFFu, rem = (c.nr >> 8) & 0xFFu;
   const bool full = gr < c.f;
-  const uint8_t* src = reinterpret_cast<const uint8_t*>(c.src + 16ull * gr);
   uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst + 16ull * gr);
   if (OPB == kBatchCtr) {
     const uint32_t ctr = c.ctr + gr;
@@ -451,22 +504,19 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
     if (full) {
       __stcs(reinterpret_cast<uint4*>(dst),
              make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3));
-    } else {  // partial last block: its leading `rem` bytes
-      for (uint32_t b = 0; b < rem; ++b) dst[b] = src[b] ^ static_cast<uint8_t>(state_byte(s, b));
+    } else {  // partial last block (v_in holds its `rem` bytes): the leading `rem` bytes
+      store_partial(dst, make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3), rem);
     }
   } else if (OPB == kBatchEcbEnc) {
     uint4 v = v_in;
-    if (!full) {  // last block: rem message bytes then PKCS#7 pad bytes (1..16 of value 16 - rem)
-      const uint32_t pad = 16 - rem;
-      uint32_t w[4];
-      for (int q = 0; q < 4; ++q) {
-        uint32_t acc = 0;
-        for (int b = 0; b < 4; ++b) {
-          const uint32_t k = 4 * q + b;
-          const uint32_t byte = k < rem ? src[k] : pad;
-          acc |= byte << (8 * b);
-        }
-        w[q] = acc;
+    if (!full) {  // last block: rem message bytes (in v_in) then PKCS#7 pad bytes of value 16 - rem
+      const uint32_t pad = (16 - rem) * 0x01010101u;
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t keep = rem >= 4 * q + 4 ? 4 : rem > 4 * q ? rem - 4 * q : 0;  // message bytes in word q
+        const uint32_t mask = keep == 4 ? 0xFFFFFFFFu : (1u << (8 * keep)) - 1;
+        w[q] = (w[q] & mask) | (pad & ~mask);
       }
       v = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -656,11 +706,11 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
           if (gr >= gr1) break;
           if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
           uint4 v = next;
-          if (!have_next && gr < c.f) v = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
+          if (!have_next) v = load_block<OPB>(c, gr);
           // load this lane's next block of the span (same message) before this one's rounds
           const uint32_t gn = gr + 32;
-          have_next = k < 7 && gn < gr1 && gn < c.f;
-          if (have_next) next = __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gn));
+          have_next = k < 7 && gn < gr1 && gn < c.e;
+          if (have_next) next = load_block<OPB>(c, gn);
           process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v, rc);
         }
       }

@@ -90,6 +90,29 @@ def test_batch_small_messages_all_key_sizes(torch, B, oracle, op):
     oracle_check(B, oracle, b, kb, keys, ivs)
 
 
+@pytest.mark.parametrize("op", [0, 1])
+def test_batch_writes_nothing_outside_messages(torch, B, oracle, op):
+    """Output bytes between messages (the 16-byte alignment gaps after ragged
+    CTR messages) keep their canary value; ECB output fills its padded length."""
+    n = 600
+    lengths = mixed_lengths(31 + op, n)
+    kb = W.key_sizes(31, n)
+    keys = W.message_keys(31, n)
+    ivs = W.message_ivs(31, n)
+    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=32)
+    b.out.fill_(0xA5)
+    b.submit()
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, b, kb, keys, ivs)
+    out = b.out.cpu().numpy()
+    written = np.zeros(out.size, bool)
+    ol = b.out_len.cpu().numpy()
+    for m in range(n):
+        o = int(b.out_off_np[m])
+        written[o: o + int(ol[m])] = True
+    assert np.all(out[~written] == 0xA5)
+
+
 def test_batch_decrypt_round_trip_and_bad_padding(torch, B, oracle):
     n = 300
     lengths = mixed_lengths(5, n)
