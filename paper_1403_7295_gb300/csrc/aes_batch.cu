@@ -5,16 +5,24 @@
 // Pipeline on the caller's stream:
 //   1. batch_count_scan  per message: validate, count 16-byte blocks
 //      (CTR ceil(len/16); ECB+PKCS#7 encrypt floor(len/16)+1; decrypt len/16),
-//      write status/out_len, exclusive-scan the counts inside chunks of 4096
-//      messages; reset the tile counter.
+//      write status/out_len, exclusive-scan the counts of long messages
+//      (kShortMax blocks or more) inside chunks of 4096 messages; reset the
+//      work counters.
 //   2. batch_scan_chunks one CTA scans the chunk totals and writes the grand total.
-//   3. batch_scan_fix    adds each chunk's offset: blk_off[m] = first global block of m.
-//   4. batch_kernel      persistent CTAs claim tiles of `tile_blocks` blocks with an
-//      atomic counter, find the tile's messages by a 32-way warp search over
-//      blk_off, expand their keys on the device into shared memory (one thread
-//      per message, FIPS-197 §5.2; the equivalent inverse schedule for ECB
-//      decryption), then run the T-table rounds of aes_ttable.cuh with round
-//      keys read from shared memory (one 128-bit broadcast load per round).
+//   3. batch_scan_fix    adds each chunk's offset: blk_off[m] = first block of m
+//      in the long-message block space.
+//   4. batch_kernel      persistent CTAs.  Long messages: the CTA claims tiles of
+//      `tile_blocks` blocks of the long-message space with an atomic counter,
+//      finds the tile's messages by a 32-way warp search over blk_off, expands
+//      their keys on the device into shared memory (one thread per message,
+//      FIPS-197 §5.2; the equivalent inverse schedule for ECB decryption), and
+//      its warps run the T-table rounds of aes_ttable.cuh with round keys read
+//      from shared memory (one 128-bit broadcast load per round).  Short
+//      messages (1 .. kShortMax-1 blocks), afterwards: every warp on its own
+//      claims groups of consecutive messages, expands their keys into its own
+//      slots and runs their blocks, with no CTA barrier (so key expansion and
+//      claims of one warp overlap the rounds of the others, and the phase fills
+//      the tail of the tile phase).
 #include "aes_batch.h"
 #include "aes_smem_attr.h"
 #include "aes_ttable.cuh"
@@ -55,6 +63,14 @@ struct Slot {
 };
 constexpr uint32_t kCtrC1 = 60, kCtrRk0w3 = 64;
 
+// Messages of fewer blocks than this go through the per-warp short phase.
+constexpr uint64_t kShortMax = 512;
+
+// Messages per warp group in the short phase: a warp's share of the window
+// slots of a 1024-thread CTA.
+template <int OPB>
+constexpr uint32_t kGroup = WindowSize<OPB>::value / 32;
+
 template <int OPB>
 constexpr size_t batch_table_bytes() {
   return OPB == kBatchEcbDec ? 192 * 1024 : 128 * 1024;
@@ -67,7 +83,11 @@ constexpr size_t batch_smem_bytes() {
 
 // ---------------------------------------------------------------- scan ----
 
-__device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m) {
+// Validation and block count of message m: its status and (for a valid
+// message) its 16-byte blocks and output length (0 for a decryption, whose
+// length is known after the padding check).  A rejected message has 0 blocks.
+__device__ __forceinline__ uint64_t message_blocks(const BatchArgs& a, uint32_t m, int32_t* status,
+                                                   uint64_t* out_len) {
   const uint64_t len = a.in_len[m];
   int32_t st = AES_OK;
   if ((a.in_off[m] | a.out_off[m]) & 15u) st = AES_ERR_ALIGN;
@@ -97,9 +117,20 @@ __device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m)
     olen = 0;  // set after the padding check
   }
   if (st != AES_OK) nb = olen = 0;
+  *status = st;
+  *out_len = olen;
+  return nb;
+}
+
+// Count-kernel step for message m: write its status and output length and
+// return its size in the long-message block space (0 for short messages).
+__device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m) {
+  int32_t st;
+  uint64_t olen;
+  const uint64_t nb = message_blocks(a, m, &st, &olen);
   if (a.status) a.status[m] = st;
   if (a.out_len) a.out_len[m] = olen;
-  return nb;
+  return nb >= kShortMax ? nb : 0;
 }
 
 // Exclusive scan of one value per thread across the CTA; *total = CTA sum.
@@ -151,7 +182,10 @@ __global__ void __launch_bounds__(kScanThreads) batch_count_scan(const BatchArgs
   if (threadIdx.x == 0) {
     a.chunk_sum[blockIdx.x] = total;
     if (gridDim.x == 1) a.blk_off[a.n] = total;
-    if (blockIdx.x == 0) *a.tile_counter = 0;
+    if (blockIdx.x == 0) {
+      *a.tile_counter = 0;
+      *a.short_counter = 0;
+    }
   }
 }
 
@@ -321,13 +355,14 @@ __device__ __forceinline__ uint32_t state_byte(const State& s, uint32_t k) {
   return (w >> (8 * (k & 3))) & 0xFFu;
 }
 
-// Fill a window slot with message m: block range, addresses, key schedule,
-// CTR constants.
+// Fill a slot with message m occupying blocks [blk_start, blk_end) of the
+// block space being worked on: block range, addresses, key schedule, CTR
+// constants.
 template <int OPB>
-__device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uint32_t sb_off,
-                          uint32_t m, Slot& sl, uint32_t* rk) {
-  sl.blk_start = a.blk_off[m];
-  sl.blk_end = a.blk_off[m + 1];
+__device__ void fill_slot(const BatchArgs& a, const Tabs& T, const char* sb, uint32_t sb_off,
+                          uint32_t m, uint64_t blk_start, uint64_t blk_end, Slot& sl, uint32_t* rk) {
+  sl.blk_start = blk_start;
+  sl.blk_end = blk_end;
   sl.msg = m;
   sl.nr = 10;
   if (sl.blk_end == sl.blk_start) return;  // empty or rejected: never selected
@@ -373,6 +408,13 @@ __device__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
       rk[kCtrC1 + j] = acc;
     }
   }
+}
+
+// A window slot of the tile phase: message m at its place in the long-message space.
+template <int OPB>
+__device__ __forceinline__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb,
+                                          uint32_t sb_off, uint32_t m, Slot& sl, uint32_t* rk) {
+  fill_slot<OPB>(a, T, sb, sb_off, m, a.blk_off[m], a.blk_off[m + 1], sl, rk);
 }
 
 // The message a thread is working in, cached in registers and rebased to the
@@ -597,6 +639,28 @@ __device__ __forceinline__ void span_fast(const BatchArgs& a, const Tabs& T, con
   }
 }
 
+// Blocks g_begin + 32k + lane < g_end of the slots' block space (tile blocks
+// t0 + gr), each in the message select_message finds for it; the lane's next
+// block is loaded before the current one's rounds when it is in the same message.
+template <int OPB>
+__device__ __forceinline__ void run_blocks(const BatchArgs& a, const Tabs& T, const Slot* slots,
+                                           const uint32_t* rk_all, uint32_t wn, uint64_t t0, uint64_t t1,
+                                           uint32_t g_begin, uint32_t g_end, uint32_t lane, Cur& c,
+                                           RunCache& rc) {
+  uint4 next = make_uint4(0, 0, 0, 0);
+  bool have_next = false;
+#pragma unroll 1
+  for (uint32_t gr = g_begin + lane; gr < g_end; gr += 32) {
+    if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
+    uint4 v = next;
+    if (!have_next) v = load_block<OPB>(c, gr);
+    const uint32_t gn = gr + 32;
+    have_next = gn < g_end && gn < c.e;
+    if (have_next) next = load_block<OPB>(c, gn);
+    process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v, rc);
+  }
+}
+
 // Warp 0: claim the next tile and find its first and last message.
 __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total,
                                            unsigned long long* s_tile, uint32_t* s_mlo,
@@ -615,6 +679,184 @@ __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total,
     *s_tile = t;
     *s_mlo = mlo;
     *s_mhi = mhi;
+  }
+}
+
+// ------------------------------------------------------ short messages ----
+//
+// After the tile phase every warp works alone on groups of kGroup consecutive
+// messages.  A group's valid short messages are numbered in order (compact
+// index ci) and laid end to end in a group block space; lane l of a warp step
+// takes group block base + l.  The message of each lane's block follows from
+// one ballot (messages starting at or before `base`) and one OR-reduction (a
+// bit for every message starting inside the step), so there is no search.
+
+// One message of a group (block numbers relative to the group).
+struct GroupMsg {
+  uint64_t src0, dst0;  // byte address of (virtual) group block 0 in the message's input / output
+  uint32_t ctr0;        // CTR: counter of group block 0; ECB: the message's first group block
+  uint32_t info;        // nr | rem << 8 | lane of the message in the group << 16
+  uint32_t full_end;    // first group block that is not a whole 16-byte input block
+  uint32_t end;         // first group block after the message
+};
+static_assert(sizeof(GroupMsg) == 32, "two 128-bit loads per record");
+
+// Per-warp region: kGroup round-key slots, kGroup records, kGroup start blocks.
+template <int OPB>
+constexpr uint32_t kWarpRegion =
+    static_cast<uint32_t>(WindowSize<OPB>::value * (kRkStride * 4 + sizeof(Slot)) / 32) & ~15u;
+static_assert(kGroup<kBatchCtr> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchCtr>, "");
+static_assert(kGroup<kBatchEcbEnc> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchEcbEnc>, "");
+static_assert(kGroup<kBatchEcbDec> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchEcbDec>, "");
+
+template <int OPB>
+__device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, const uint32_t* wrk,
+                                            const GroupMsg& r, uint32_t gr, unsigned long long m0) {
+  const uint32_t nr = r.info & 0xFFu, rem = (r.info >> 8) & 0xFFu, j = r.info >> 16;
+  const uint32_t* rk = wrk + j * kRkStride;
+  const bool full = gr < r.full_end;
+  const uint8_t* src = reinterpret_cast<const uint8_t*>(r.src0 + 16ull * gr);
+  uint8_t* dst = reinterpret_cast<uint8_t*>(r.dst0 + 16ull * gr);
+  uint4 v;
+  if (OPB == kBatchEcbDec || full) v = __ldcs(reinterpret_cast<const uint4*>(src));
+  else v = load_partial(src, rem);
+  if (OPB == kBatchCtr) {
+    const uint32_t x = __byte_perm(r.ctr0 + gr, 0, 0x0123) ^ rk[kCtrRk0w3];
+    const uint4 c1 = lds128(rk + kCtrC1);
+    State s{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
+    s = enc_any(T, s, rk, nr, 2);
+    const uint4 o = make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3);
+    if (full) __stcs(reinterpret_cast<uint4*>(dst), o);
+    else store_partial(dst, o, rem);
+  } else if (OPB == kBatchEcbEnc) {
+    if (!full) {  // last block: rem message bytes then PKCS#7 pad bytes of value 16 - rem
+      const uint32_t pad = (16 - rem) * 0x01010101u;
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t keep = rem >= 4 * q + 4 ? 4 : rem > 4 * q ? rem - 4 * q : 0;
+        const uint32_t mask = keep == 4 ? 0xFFFFFFFFu : (1u << (8 * keep)) - 1;
+        w[q] = (w[q] & mask) | (pad & ~mask);
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    const uint4 k0 = lds128(rk);
+    State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+    s = enc_any(T, s, rk, nr, 1);
+    __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
+  } else {
+    const uint4 k0 = lds128(rk);
+    State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
+    s = dec_any(T, s, rk, nr);
+    __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
+    if (gr + 1 == r.end) {  // the message's last block: check PKCS#7
+      const uint32_t p = state_byte(s, 15);
+      bool ok = p >= 1 && p <= 16;
+      for (uint32_t q = 16 - (ok ? p : 0); q < 16; ++q) ok = ok && state_byte(s, q) == p;
+      const uint32_t m = static_cast<uint32_t>(m0 + j);
+      if (a.status) a.status[m] = ok ? AES_OK : AES_ERR_PADDING;
+      if (a.out_len) a.out_len[m] = ok ? 16ull * (r.end - r.ctr0) - p : 0;
+    }
+  }
+}
+
+template <int OPB>
+__device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, uint32_t sb_off,
+                            char* region, uint32_t warp, uint32_t lane) {
+  constexpr uint32_t G = kGroup<OPB>;
+  char* wbase = region + warp * kWarpRegion<OPB>;
+  uint32_t* wrk = reinterpret_cast<uint32_t*>(wbase);
+  GroupMsg* rec = reinterpret_cast<GroupMsg*>(wbase + G * kRkStride * 4);
+  uint32_t* first = reinterpret_cast<uint32_t*>(wbase + G * (kRkStride * 4 + sizeof(GroupMsg)));
+  unsigned long long m0 = 0;
+  if (lane == 0) m0 = atomicAdd(a.short_counter, static_cast<unsigned long long>(G));
+  m0 = __shfl_sync(0xffffffffu, m0, 0);
+  while (m0 < a.n) {
+    unsigned long long m1 = 0;  // the next group, claimed now so its latency overlaps this one
+    if (lane == 0) m1 = atomicAdd(a.short_counter, static_cast<unsigned long long>(G));
+    uint32_t nb = 0;
+    uint64_t len = 0;
+    if (lane < G && m0 + lane < a.n) {
+      int32_t st;
+      uint64_t olen;
+      const uint64_t b = message_blocks(a, static_cast<uint32_t>(m0 + lane), &st, &olen);
+      if (st == AES_OK && b > 0 && b < kShortMax) {
+        nb = static_cast<uint32_t>(b);
+        len = a.in_len[m0 + lane];
+      }
+    }
+    const uint32_t valid = __ballot_sync(0xffffffffu, nb > 0);
+    uint32_t incl = nb;  // inclusive prefix of the group's block counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= static_cast<uint32_t>(o)) incl += y;
+    }
+    const uint32_t nblk = __shfl_sync(0xffffffffu, incl, 31);
+    if (nb > 0) {
+      const uint32_t m = static_cast<uint32_t>(m0 + lane);
+      const uint32_t b0 = incl - nb;
+      const uint32_t ci = __popc(valid & ((1u << lane) - 1));
+      uint32_t* rk = wrk + lane * kRkStride;
+      uint32_t nr;
+      if (a.keys != nullptr) {
+        const uint32_t nk = a.key_bits[m] / 32;
+        nr = nk + 6;
+        expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, rk);
+        if (OPB == kBatchEcbDec) to_decrypt_schedule(T, sb, sb_off, nr, rk);
+      } else {
+        const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
+        nr = ks.nr;
+        const uint32_t* src = OPB == kBatchEcbDec ? ks.rk_dec : ks.rk_enc;
+        const uint32_t nw = 4 * (nr + 1);
+#pragma unroll
+        for (uint32_t i = 0; i < 60; ++i)
+          if (i < nw) rk[i] = __ldg(src + i);
+      }
+      GroupMsg r;
+      r.src0 = reinterpret_cast<uint64_t>(a.in) + a.in_off[m] - 16ull * b0;
+      r.dst0 = reinterpret_cast<uint64_t>(a.out) + a.out_off[m] - 16ull * b0;
+      r.ctr0 = b0;
+      if (OPB == kBatchCtr) {
+        const uint4 ivw = *reinterpret_cast<const uint4*>(a.iv + 16ull * m);
+        r.ctr0 = __byte_perm(ivw.w, 0, 0x0123) - b0;
+        const uint32_t s0 = ivw.x ^ rk[0], s1 = ivw.y ^ rk[1], s2 = ivw.z ^ rk[2];
+        rk[kCtrRk0w3] = rk[3];
+        // round-1 columns without the counter column's lookups (column 3 of the state)
+        rk[kCtrC1 + 0] = rk[4] ^ T.t0(s0) ^ T.t1(s1) ^ T.t2(s2);
+        rk[kCtrC1 + 1] = rk[5] ^ T.t0(s1) ^ T.t1(s2) ^ T.t3(s0);
+        rk[kCtrC1 + 2] = rk[6] ^ T.t0(s2) ^ T.t2(s0) ^ T.t3(s1);
+        rk[kCtrC1 + 3] = rk[7] ^ T.t1(s0) ^ T.t2(s1) ^ T.t3(s2);
+      }
+      r.info = nr | static_cast<uint32_t>(len & 15u) << 8 | lane << 16;
+      r.full_end = b0 + static_cast<uint32_t>(len / 16);
+      r.end = incl;
+      rec[ci] = r;
+      first[ci] = b0;
+    }
+    __syncwarp();
+    const uint32_t ng = __popc(valid);
+    const uint32_t my_first = lane < ng ? first[lane] : 0xFFFFFFFFu;
+    uint32_t cur = 0xFFFFFFFFu;
+    GroupMsg r{};
+#pragma unroll 1
+    for (uint32_t base = 0; base < nblk; base += 32) {
+      const uint32_t gr = base + lane;
+      // messages starting at or before `base`, and a bit for each start inside the step
+      const uint32_t c0 = __popc(__ballot_sync(0xffffffffu, my_first <= base)) - 1;
+      const uint32_t d = my_first - base;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, (my_first > base && d < 32) ? 1u << d : 0u);
+      const uint32_t ci = c0 + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
+      if (gr < nblk) {
+        if (ci != cur) {
+          cur = ci;
+          r = rec[ci];
+        }
+        short_block<OPB>(a, T, wrk, r, gr, m0);
+      }
+    }
+    __syncwarp();  // the slots are refilled next
+    m0 = __shfl_sync(0xffffffffu, m1, 0);
   }
 }
 
@@ -673,8 +915,6 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
       const uint32_t gr1 = static_cast<uint32_t>(min(t1, slots[wn - 1].blk_end) - t0);
       Cur c{1, 0, 0, 0, 0, 0, 0, 0};  // empty: the first block selects its message
       RunCache rc{0, 0, 0, 0, 0, 0, 0, 0};
-      uint4 next = make_uint4(0, 0, 0, 0);
-      bool have_next = false;
       // Warps claim spans of 256 consecutive blocks from a shared counter (so
       // they finish the window together); lane l takes blocks 32k + l of the
       // span (coalesced), so a lane's blocks share counter runs.
@@ -684,7 +924,6 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
         sp = __shfl_sync(0xffffffffu, sp, 0);
         const uint32_t span = gr0 + sp * 256;
         if (span >= gr1) break;
-        have_next = false;
         if (span + 256 <= gr1) {
           // every lane takes the message of the span's first block; if that
           // message holds the whole span in whole blocks, run the fast loop
@@ -701,22 +940,13 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
             continue;
           }
         }
-        for (uint32_t k = 0; k < 8; ++k) {
-          const uint32_t gr = span + 32 * k + lane;
-          if (gr >= gr1) break;
-          if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
-          uint4 v = next;
-          if (!have_next) v = load_block<OPB>(c, gr);
-          // load this lane's next block of the span (same message) before this one's rounds
-          const uint32_t gn = gr + 32;
-          have_next = k < 7 && gn < gr1 && gn < c.e;
-          if (have_next) next = load_block<OPB>(c, gn);
-          process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v, rc);
-        }
+        run_blocks<OPB>(a, T, slots, rk_all, wn, t0, t1, span, min(span + 256, gr1), lane, c, rc);
       }
       __syncthreads();
     }
   }
+
+  short_phase<OPB>(a, T, sb, sb_off, reinterpret_cast<char*>(rk_all), warp, lane);
 }
 
 template <int OPB>
@@ -749,6 +979,7 @@ void batch_bind_workspace(BatchArgs* a, void* ws) {
   a->chunk_sum = reinterpret_cast<uint64_t*>(p);
   p += up(8 * (nchunks > 0 ? nchunks : 1));
   a->tile_counter = reinterpret_cast<unsigned long long*>(p);
+  a->short_counter = a->tile_counter + 1;
   a->nchunks = static_cast<uint32_t>(nchunks);
 }
 

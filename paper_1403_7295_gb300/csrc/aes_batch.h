@@ -32,7 +32,8 @@ struct BatchArgs {
   // workspace
   uint64_t* blk_off;    // [n + 1] first global block of each message; [n] = total
   uint64_t* chunk_sum;  // [nchunks] per-chunk totals, then chunk offsets
-  unsigned long long* tile_counter;
+  unsigned long long* tile_counter;   // next tile of the long-message block space
+  unsigned long long* short_counter;  // next group of messages for the short-message phase
   uint32_t nchunks;
 };
 

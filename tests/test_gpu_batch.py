@@ -72,8 +72,14 @@ def oracle_check(B, oracle, batch, key_bits, keys, ivs, idx=None, check_status=T
                 assert status[m] == 6 and out_len[m] == 0, m
 
 
+# Messages below 512 blocks take the per-warp short phase, the others the tile
+# phase: these lengths sit on both sides of that split for every op (ECB
+# encryption adds a padding block, so 8175 / 8176 bytes fall on either side).
+SPLIT = [8175, 8176, 8177, 8191, 8192, 8193, 8208, 20000, 70001]
+
+
 def mixed_lengths(seed, n):
-    special = np.array([0, 1, 15, 16, 17, 31, 32, 33, 255, 256, 4095, 4096, 4097], np.uint64)
+    special = np.array([0, 1, 15, 16, 17, 31, 32, 33, 255, 256, 4095, 4096, 4097] + SPLIT, np.uint64)
     rest = W.uniform_lengths(seed, n - special.size, 0, 5000)
     return np.concatenate([special, rest])
 
@@ -179,6 +185,30 @@ def test_batch_many_tiny_messages_multi_window(torch, B, oracle):
     ivs = W.message_ivs(9, n)
     b = build(B, torch, 0, lengths, kb, keys, ivs, seed=14)
     for cfg in (None, B.AesBatchConfig(256, 256, 0, 0), B.AesBatchConfig(1024, 32768, 3, 0)):
+        b.out.fill_(0)
+        b.submit(config=cfg)
+        torch.cuda.synchronize()
+        oracle_check(B, oracle, b, kb, keys, ivs)
+
+
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_batch_long_messages_among_many_short(torch, B, oracle, op):
+    """Long messages (>= 512 blocks) each followed by 300 short ones: a tile's
+    message range then spans several key windows (most slots empty), and the
+    short phase runs beside the tile phase."""
+    n_long, gap = 12, 300
+    longs = W.uniform_lengths(41, n_long, 8192, 40000)
+    shorts = W.uniform_lengths(42, n_long * gap, 0, 600)
+    lengths = np.concatenate([np.concatenate([[longs[i]], shorts[i * gap:(i + 1) * gap]])
+                              for i in range(n_long)]).astype(np.uint64)
+    if op == 2:
+        lengths = np.maximum((lengths // np.uint64(16)) * np.uint64(16), np.uint64(16))
+    n = lengths.size
+    kb = W.key_sizes(41, n)
+    keys = W.message_keys(41, n)
+    ivs = W.message_ivs(41, n, counter0=0xFFFFFF80)
+    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=43)
+    for cfg in (None, B.AesBatchConfig(1024, 65536, 0, 0), B.AesBatchConfig(512, 1024, 5, 0)):
         b.out.fill_(0)
         b.submit(config=cfg)
         torch.cuda.synchronize()
