@@ -350,6 +350,59 @@ __device__ __forceinline__ State dec_any(const Tabs& T, State s, const uint32_t*
   }
 }
 
+// Rounds for a warp whose lanes may hold keys of different sizes.  Rounds
+// 1..9 are full rounds for every key size; rounds 10..13 run up to the
+// warp's largest round count, each lane masked to its own, then every lane
+// takes its final round.  One compact body serves all sizes: per-size
+// unrolled copies interleaved in one warp thrash the instruction cache.
+__device__ __forceinline__ State enc_lanes(const Tabs& T, State s, const uint32_t* rk, uint32_t nr,
+                                           int first) {
+  const uint32_t nr_max = __reduce_max_sync(__activemask(), nr);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    if (r < first) continue;
+    const uint4 k = lds128(rk + 4 * r);
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+    enc_round(T, s, kk);
+  }
+#pragma unroll
+  for (int r = 10; r < 14; ++r) {
+    if (static_cast<uint32_t>(r) >= nr_max) break;
+    if (static_cast<uint32_t>(r) < nr) {
+      const uint4 k = lds128(rk + 4 * r);
+      const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+      enc_round(T, s, kk);
+    }
+  }
+  const uint4 k = lds128(rk + 4 * nr);
+  const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+  enc_final(T, s, kk);
+  return s;
+}
+
+__device__ __forceinline__ State dec_lanes(const Tabs& T, State s, const uint32_t* rk, uint32_t nr) {
+  const uint32_t nr_max = __reduce_max_sync(__activemask(), nr);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint4 k = lds128(rk + 4 * r);
+    const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+    dec_round(T, s, kk);
+  }
+#pragma unroll
+  for (int r = 10; r < 14; ++r) {
+    if (static_cast<uint32_t>(r) >= nr_max) break;
+    if (static_cast<uint32_t>(r) < nr) {
+      const uint4 k = lds128(rk + 4 * r);
+      const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+      dec_round(T, s, kk);
+    }
+  }
+  const uint4 k = lds128(rk + 4 * nr);
+  const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+  dec_final(T, s, kk);
+  return s;
+}
+
 __device__ __forceinline__ uint32_t state_byte(const State& s, uint32_t k) {
   const uint32_t w = k < 4 ? s.s0 : k < 8 ? s.s1 : k < 12 ? s.s2 : s.s3;
   return (w >> (8 * (k & 3))) & 0xFFu;
@@ -701,19 +754,31 @@ struct GroupMsg {
 };
 static_assert(sizeof(GroupMsg) == 32, "two 128-bit loads per record");
 
+// Words per round-key slot in the short phase.  CTR slots add, after the
+// round keys (0..59) and the folded round-1 columns (60..63): word 64 the
+// round-0 key word 3, 65 the cached counter run (counter >> 8), 66 that run's
+// column-3 input xr, 67 its round-1 column 0 without the counter byte, and
+// 68..71 its round-2 columns without the column-0 term.
+template <int OPB>
+constexpr uint32_t kShortStride = OPB == kBatchCtr ? 72 : kRkStride;
+constexpr uint32_t kRunWords = 64, kRunD = 68;
+
 // Per-warp region: kGroup round-key slots, kGroup records, kGroup start blocks.
 template <int OPB>
 constexpr uint32_t kWarpRegion =
     static_cast<uint32_t>(WindowSize<OPB>::value * (kRkStride * 4 + sizeof(Slot)) / 32) & ~15u;
-static_assert(kGroup<kBatchCtr> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchCtr>, "");
-static_assert(kGroup<kBatchEcbEnc> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchEcbEnc>, "");
-static_assert(kGroup<kBatchEcbDec> * (kRkStride * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<kBatchEcbDec>, "");
+template <int OPB>
+constexpr bool region_fits() {
+  return kGroup<OPB> * (kShortStride<OPB> * 4 + sizeof(GroupMsg) + 4) <= kWarpRegion<OPB>;
+}
+static_assert(region_fits<kBatchCtr>() && region_fits<kBatchEcbEnc>() && region_fits<kBatchEcbDec>(),
+              "short-phase groups exceed a warp's share of the window region");
 
 template <int OPB>
 __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, const uint32_t* wrk,
                                             const GroupMsg& r, uint32_t gr, unsigned long long m0) {
   const uint32_t nr = r.info & 0xFFu, rem = (r.info >> 8) & 0xFFu, j = r.info >> 16;
-  const uint32_t* rk = wrk + j * kRkStride;
+  const uint32_t* rk = wrk + j * kShortStride<OPB>;
   const bool full = gr < r.full_end;
   const uint8_t* src = reinterpret_cast<const uint8_t*>(r.src0 + 16ull * gr);
   uint8_t* dst = reinterpret_cast<uint8_t*>(r.dst0 + 16ull * gr);
@@ -721,10 +786,21 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
   if (OPB == kBatchEcbDec || full) v = __ldcs(reinterpret_cast<const uint4*>(src));
   else v = load_partial(src, rem);
   if (OPB == kBatchCtr) {
-    const uint32_t x = __byte_perm(r.ctr0 + gr, 0, 0x0123) ^ rk[kCtrRk0w3];
-    const uint4 c1 = lds128(rk + kCtrC1);
-    State s{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
-    s = enc_any(T, s, rk, nr, 2);
+    const uint32_t ctr = r.ctr0 + gr;
+    const uint4 q = lds128(rk + kRunWords);  // rk0 word 3, cached run, xr, c10
+    uint32_t xr = q.z;
+    uint4 d = lds128(rk + kRunD);
+    if ((ctr >> 8) != q.y) {  // outside the cached run: that run's constants (15 lookups)
+      xr = __byte_perm(ctr & ~255u, 0, 0x0123) ^ q.x;
+      const uint4 c1 = lds128(rk + kCtrC1), k2 = lds128(rk + 8);
+      const uint32_t s1 = c1.y ^ T.t2(xr), s2 = c1.z ^ T.t1(xr), s3 = c1.w ^ T.t0(xr);
+      d = make_uint4(k2.x ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3), k2.y ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3),
+                     k2.z ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1), k2.w ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2));
+    }
+    // rounds 1-2: only round-1 column 0 depends on the counter's low byte
+    const uint32_t s0 = q.w ^ T.t3(xr ^ ((ctr & 255u) << 24));
+    State s{d.x ^ T.t0(s0), d.y ^ T.t3(s0), d.z ^ T.t2(s0), d.w ^ T.t1(s0)};
+    s = enc_lanes(T, s, rk, nr, 3);
     const uint4 o = make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3);
     if (full) __stcs(reinterpret_cast<uint4*>(dst), o);
     else store_partial(dst, o, rem);
@@ -742,12 +818,12 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
     }
     const uint4 k0 = lds128(rk);
     State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-    s = enc_any(T, s, rk, nr, 1);
+    s = enc_lanes(T, s, rk, nr, 1);
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
   } else {
     const uint4 k0 = lds128(rk);
     State s{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-    s = dec_any(T, s, rk, nr);
+    s = dec_lanes(T, s, rk, nr);
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(s.s0, s.s1, s.s2, s.s3));
     if (gr + 1 == r.end) {  // the message's last block: check PKCS#7
       const uint32_t p = state_byte(s, 15);
@@ -766,8 +842,8 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
   constexpr uint32_t G = kGroup<OPB>;
   char* wbase = region + warp * kWarpRegion<OPB>;
   uint32_t* wrk = reinterpret_cast<uint32_t*>(wbase);
-  GroupMsg* rec = reinterpret_cast<GroupMsg*>(wbase + G * kRkStride * 4);
-  uint32_t* first = reinterpret_cast<uint32_t*>(wbase + G * (kRkStride * 4 + sizeof(GroupMsg)));
+  GroupMsg* rec = reinterpret_cast<GroupMsg*>(wbase + G * kShortStride<OPB> * 4);
+  uint32_t* first = reinterpret_cast<uint32_t*>(wbase + G * (kShortStride<OPB> * 4 + sizeof(GroupMsg)));
   unsigned long long m0 = 0;
   if (lane == 0) m0 = atomicAdd(a.short_counter, static_cast<unsigned long long>(G));
   m0 = __shfl_sync(0xffffffffu, m0, 0);
@@ -797,7 +873,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       const uint32_t m = static_cast<uint32_t>(m0 + lane);
       const uint32_t b0 = incl - nb;
       const uint32_t ci = __popc(valid & ((1u << lane) - 1));
-      uint32_t* rk = wrk + lane * kRkStride;
+      uint32_t* rk = wrk + lane * kShortStride<OPB>;
       uint32_t nr;
       if (a.keys != nullptr) {
         const uint32_t nk = a.key_bits[m] / 32;
@@ -827,6 +903,21 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
         rk[kCtrC1 + 1] = rk[5] ^ T.t0(s1) ^ T.t1(s2) ^ T.t3(s0);
         rk[kCtrC1 + 2] = rk[6] ^ T.t0(s2) ^ T.t2(s0) ^ T.t3(s1);
         rk[kCtrC1 + 3] = rk[7] ^ T.t1(s0) ^ T.t2(s1) ^ T.t3(s2);
+        // the counter run holding most of the message's blocks (a message of
+        // < 512 blocks spans at most three runs): its round-1/2 constants
+        const uint32_t c_first = r.ctr0 + b0;
+        const uint32_t in_first = 256 - (c_first & 255u);
+        const uint32_t run = (c_first >> 8) + (nb > 2 * in_first ? 1 : 0);
+        const uint32_t xr = __byte_perm(run << 8, 0, 0x0123) ^ rk[3];
+        const uint32_t c1y = rk[kCtrC1 + 1] ^ T.t2(xr), c1z = rk[kCtrC1 + 2] ^ T.t1(xr),
+                       c1w = rk[kCtrC1 + 3] ^ T.t0(xr);
+        rk[kRunWords + 1] = run;
+        rk[kRunWords + 2] = xr;
+        rk[kRunWords + 3] = rk[kCtrC1 + 0];
+        rk[kRunD + 0] = rk[8] ^ T.t1(c1y) ^ T.t2(c1z) ^ T.t3(c1w);
+        rk[kRunD + 1] = rk[9] ^ T.t0(c1y) ^ T.t1(c1z) ^ T.t2(c1w);
+        rk[kRunD + 2] = rk[10] ^ T.t0(c1z) ^ T.t1(c1w) ^ T.t3(c1y);
+        rk[kRunD + 3] = rk[11] ^ T.t0(c1w) ^ T.t2(c1y) ^ T.t3(c1z);
       }
       r.info = nr | static_cast<uint32_t>(len & 15u) << 8 | lane << 16;
       r.full_end = b0 + static_cast<uint32_t>(len / 16);

@@ -215,6 +215,20 @@ def test_batch_long_messages_among_many_short(torch, B, oracle, op):
         oracle_check(B, oracle, b, kb, keys, ivs)
 
 
+def test_batch_short_ctr_random_counters(torch, B, oracle):
+    """Short CTR messages whose counters start anywhere: many cross a run of
+    256 counters (and some wrap the 32-bit counter) inside the message."""
+    n = 3000
+    lengths = W.uniform_lengths(51, n, 1, 8000)
+    kb = W.key_sizes(51, n)
+    keys = W.message_keys(51, n)
+    ivs = synth.bytes_np(51, synth.STREAM_NONCE, 16 * n).reshape(n, 16)
+    ivs[::7, 12:16] = 0xFF  # counter 2^32 - 1: wraps after the first block
+    b = build(B, torch, 0, lengths, kb, keys, ivs, seed=52).submit()
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, b, kb, keys, ivs)
+
+
 def test_batch_per_message_errors(torch, B, oracle):
     n = 64
     lengths = mixed_lengths(10, n)
