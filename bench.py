@@ -194,6 +194,27 @@ def launch(A, mode, ks, iv, x, y, cfg, stream=None):
     return A.aes_ecb_decrypt(ks, x, y, stream=stream, config=cfg)
 
 
+def per_step_stats(torch, fn, n):
+    """Per-call CUDA-event times of n calls (after the timed region): median,
+    p99, and the paper's averaging (repeat, drop the runs that deviate most,
+    average the rest), read as: drop samples more than 3 median absolute
+    deviations from the median."""
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = np.array([a.elapsed_time(b) for a, b in ev])
+    med = float(np.median(t))
+    mad = float(np.median(np.abs(t - med)))
+    keep = t[np.abs(t - med) <= 3 * mad] if mad > 0 else t
+    return {"n": n, "median_ms": round(med, 5), "p99_ms": round(float(np.percentile(t, 99)), 5),
+            "paper_mean_ms": round(float(keep.mean()), 5), "paper_mean_kept": int(keep.size),
+            "min_ms": round(float(t.min()), 5), "max_ms": round(float(t.max()), 5)}
+
+
 def time_device(torch, fn, steps, warmup, barrier=None):
     """CUDA-event time of `steps` calls of fn() on the current stream (ms total)."""
     for _ in range(warmup):
@@ -265,6 +286,7 @@ def gpu_arm(args):
     ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), args.steps, args.warmup,
                      barrier)
     clocks = sampler.stop() if sampler else None
+    dist_steps = per_step_stats(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), min(args.steps, 200))
     t = torch.tensor([ms], device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -321,6 +343,10 @@ def gpu_arm(args):
             rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
                                  f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
         result["roofline"] = rl
+        dist_steps["gbps_at_median"] = round(nbytes / (dist_steps["median_ms"] / 1e3) / 1e9, 2)
+        dist_steps["how"] = ("one event pair per launch, after the timed region (rank 0); the timed "
+                             "value above is the event span over all steps")
+        result["per_step"] = dist_steps
         result["probes_ops_per_clk_per_sm"] = probes
         result["clocks"] = clocks
         result["context"] = {"paper_best_cpu_gbps": round(PAPER_BEST_GBPS, 3),

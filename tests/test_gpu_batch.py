@@ -229,6 +229,27 @@ def test_batch_short_ctr_random_counters(torch, B, oracle):
     oracle_check(B, oracle, b, kb, keys, ivs)
 
 
+def test_batch_modes_in_flight_together(torch, B, oracle):
+    """Mixed-mode run: a CTR batch and an ECB+PKCS#7 batch of the same
+    messages, submitted alternately on two streams so both are in flight at
+    once, three times; every message of both equals the oracle."""
+    n = 700
+    lengths = mixed_lengths(61, n)
+    kb = W.key_sizes(61, n)
+    keys = W.message_keys(61, n)
+    ivs = W.message_ivs(61, n)
+    ctr = build(B, torch, 0, lengths, kb, keys, ivs, seed=62)
+    ecb = build(B, torch, 1, lengths, kb, keys, None, seed=62)
+    torch.cuda.synchronize()  # inputs and descriptors were written on the default stream
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(3):
+        ctr.submit(stream=s1)
+        ecb.submit(stream=s2)
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, ctr, kb, keys, ivs)
+    oracle_check(B, oracle, ecb, kb, keys, None)
+
+
 def test_batch_per_message_errors(torch, B, oracle):
     n = 64
     lengths = mixed_lengths(10, n)
