@@ -24,6 +24,10 @@ struct CtrParams {
   uint32_t rk0w3;   // round-0 key word 3
   uint32_t c1[4];   // folded round-1 columns (round-1 key included)
   uint32_t iv_w[4]; // IV words (little-endian), used by the partial tail block
+  // run-cached CTR kernel only, set at launch for its grid: runs done one per
+  // warp in whole waves, and log2 of the pieces each later run is split into
+  uint64_t whole_runs;
+  uint32_t tail_shift;
 };
 
 struct LaunchShape {

@@ -216,6 +216,62 @@ __global__ void __launch_bounds__(1024, 1)
 // (k = 0..7, coalesced 512-byte accesses per k); each lane computes the run's
 // constants once (3 + 12 lookups) and then spends 1 + 4 lookups per block on
 // rounds 1-2 instead of 4 + 16.
+//
+// Runs that fill whole waves of the grid's warps go one per warp.  The runs
+// of the last, partial wave are split into ctr_tail_pieces() pieces of 8/P
+// steps each, so that every warp has work there (each piece computes its
+// run's constants).  The launch computes the split for its grid
+// (CtrParams::whole_runs, tail_shift).
+__host__ __device__ __forceinline__ uint32_t ctr_tail_pieces(uint64_t tail_runs, uint64_t warps) {
+  if (tail_runs == 0) return 1;
+  const uint64_t q = warps / tail_runs;
+  return q >= 8 ? 8 : q >= 4 ? 4 : q >= 2 ? 2 : 1;
+}
+
+// Steps [k0, k1) of one run.  kWhole: the whole run (k0 = 0, k1 = 8, known
+// at compile time, unrolled by two); otherwise a piece, not unrolled.
+template <int NR, bool kWhole>
+__device__ __forceinline__ void ctr_run_steps(const Tabs& T, const uint4* in, uint4* out,
+                                              uint64_t nblocks, uint64_t units, uint32_t tail_bytes,
+                                              const RoundKeys& rk, const CtrParams& cp, uint32_t off0,
+                                              uint64_t run, uint32_t k0, uint32_t k1, uint32_t lane) {
+  if (kWhole) {
+    k0 = 0;
+    k1 = 8;
+  }
+  // counter of position 0 of this run (modulo 2^32); its low byte is 0
+  const uint32_t ctr_run = (cp.ctr0 & ~255u) + static_cast<uint32_t>(run) * 256u;
+  const uint32_t xr = __byte_perm(ctr_run, 0, 0x0123) ^ cp.rk0w3;  // byte 3 still to add
+  const uint32_t s1 = cp.c1[1] ^ T.t2(xr), s2 = cp.c1[2] ^ T.t1(xr), s3 = cp.c1[3] ^ T.t0(xr);
+  const uint32_t d0 = rk.w[8] ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
+  const uint32_t d1 = rk.w[9] ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
+  const uint32_t d2 = rk.w[10] ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
+  const uint32_t d3 = rk.w[11] ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
+  const int64_t first = static_cast<int64_t>(run) * 256 - off0;  // block index of position 0
+#pragma unroll(kWhole ? 2 : 1)
+  for (uint32_t k = k0; k < k1; ++k) {
+    const uint32_t t = 32 * k + lane;
+    const int64_t idx = first + t;
+    if (idx < 0 || static_cast<uint64_t>(idx) >= units) continue;
+    const bool full = static_cast<uint64_t>(idx) < nblocks;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (full) v = __ldcs(in + idx);
+    const uint32_t s0 = cp.c1[0] ^ T.t3(xr ^ (t << 24));
+    State s{d0 ^ T.t0(s0), d1 ^ T.t3(s0), d2 ^ T.t2(s0), d3 ^ T.t1(s0)};
+    encrypt_rounds<NR>(T, s, rk, 3);
+    if (full) {
+      __stcs(out + idx, xor4(v, s));
+    } else {  // partial last block: its leading keystream bytes
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
+      uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
+      for (uint32_t b = 0; b < tail_bytes; ++b) {
+        const uint32_t w = b < 4 ? s.s0 : b < 8 ? s.s1 : b < 12 ? s.s2 : s.s3;
+        dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
+      }
+    }
+  }
+}
+
 template <int NR>
 __global__ void __launch_bounds__(1024, 1)
     ttable_ctr_cached_kernel(const uint4* in, uint4* out, uint64_t nblocks, uint32_t tail_bytes,
@@ -232,39 +288,15 @@ __global__ void __launch_bounds__(1024, 1)
   const uint64_t units = nblocks + (tail_bytes ? 1 : 0);
   const uint64_t runs = (units + off0 + 255) / 256;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (uint64_t run = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       run < runs; run += warps) {
-    // counter of position 0 of this run (modulo 2^32); its low byte is 0
-    const uint32_t ctr_run = (cp.ctr0 & ~255u) + static_cast<uint32_t>(run) * 256u;
-    const uint32_t xr = __byte_perm(ctr_run, 0, 0x0123) ^ cp.rk0w3;  // byte 3 still to add
-    const uint32_t s1 = cp.c1[1] ^ T.t2(xr), s2 = cp.c1[2] ^ T.t1(xr), s3 = cp.c1[3] ^ T.t0(xr);
-    const uint32_t d0 = rk.w[8] ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
-    const uint32_t d1 = rk.w[9] ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
-    const uint32_t d2 = rk.w[10] ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
-    const uint32_t d3 = rk.w[11] ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
-    const int64_t first = static_cast<int64_t>(run) * 256 - off0;  // block index of position 0
-#pragma unroll 2
-    for (uint32_t k = 0; k < 8; ++k) {
-      const uint32_t t = 32 * k + lane;
-      const int64_t idx = first + t;
-      if (idx < 0 || static_cast<uint64_t>(idx) >= units) continue;
-      const bool full = static_cast<uint64_t>(idx) < nblocks;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (full) v = __ldcs(in + idx);
-      const uint32_t s0 = cp.c1[0] ^ T.t3(xr ^ (t << 24));
-      State s{d0 ^ T.t0(s0), d1 ^ T.t3(s0), d2 ^ T.t2(s0), d3 ^ T.t1(s0)};
-      encrypt_rounds<NR>(T, s, rk, 3);
-      if (full) {
-        __stcs(out + idx, xor4(v, s));
-      } else {  // partial last block: its leading keystream bytes
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
-        uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
-        for (uint32_t b = 0; b < tail_bytes; ++b) {
-          const uint32_t w = b < 4 ? s.s0 : b < 8 ? s.s1 : b < 12 ? s.s2 : s.s3;
-          dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
-        }
-      }
-    }
+  const uint64_t wid = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t whole = cp.whole_runs;  // runs in full waves (runs - runs mod warps)
+  for (uint64_t run = wid; run < whole; run += warps)
+    ctr_run_steps<NR, true>(T, in, out, nblocks, units, tail_bytes, rk, cp, off0, run, 0, 8, lane);
+  const uint32_t shift = cp.tail_shift, steps = 8u >> shift;
+  for (uint64_t piece = wid; piece < ((runs - whole) << shift); piece += warps) {
+    const uint32_t k0 = (static_cast<uint32_t>(piece) & ((1u << shift) - 1)) * steps;
+    ctr_run_steps<NR, false>(T, in, out, nblocks, units, tail_bytes, rk, cp, off0, whole + (piece >> shift),
+                             k0, k0 + steps, lane);
   }
 }
 

@@ -15,14 +15,22 @@ cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint3
   auto kern = ttable_ctr_cached_kernel<NR>;
   cudaError_t e = ensure_dynamic_smem(kern, kTtableSmemEnc);
   if (e != cudaSuccess) return e;
-  // one warp per run of 256 blocks: no more CTAs than runs / warps per CTA
+  // one warp per run of 256 blocks, or per piece of a run when the runs do
+  // not fill the grid's warps: no more CTAs than those work units need
   const uint64_t runs = (nblocks + (tail ? 1 : 0) + (cp.ctr0 & 255u) + 255) / 256;
   const uint64_t warps_per_cta = shape.cta_threads / 32;
   uint64_t grid = shape.grid_ctas;
-  const uint64_t needed = (runs + warps_per_cta - 1) / warps_per_cta;
+  const uint64_t max_warps = grid * warps_per_cta;
+  const uint64_t work = runs >= max_warps ? max_warps : runs * ctr_tail_pieces(runs, max_warps);
+  const uint64_t needed = (work + warps_per_cta - 1) / warps_per_cta;
   if (grid > needed) grid = needed > 0 ? needed : 1;
+  CtrParams p = cp;
+  const uint64_t warps = grid * warps_per_cta;
+  p.whole_runs = runs - runs % warps;
+  const uint32_t pieces = ctr_tail_pieces(runs - p.whole_runs, warps);
+  p.tail_shift = pieces == 8 ? 3 : pieces == 4 ? 2 : pieces == 2 ? 1 : 0;
   kern<<<static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream>>>(
-      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
+      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, p);
   return cudaGetLastError();
 }
 
