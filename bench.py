@@ -661,8 +661,8 @@ def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
 
 def file_pipeline(torch, nbytes: int = 4 << 30) -> dict:
     """The paper's workload end to end: a file of seeded bytes encrypted into
-    another file (AES-128 CTR) through the pinned-buffer pipeline; the files
-    live in /dev/shm when it exists, so the figure is not disk-bound."""
+    another file (AES-128 CTR) through the native pipeline; the files live in
+    /dev/shm when it exists, so the figure is not disk-bound."""
     import tempfile
 
     from paper_1403_7295_gb300.filecrypt import crypt_file
@@ -673,10 +673,17 @@ def file_pipeline(torch, nbytes: int = 4 << 30) -> dict:
         x = synth.bytes_torch(12, synth.STREAM_DATA, nbytes, device="cuda")
         x.cpu().numpy().tofile(src)
         del x
-        r = crypt_file(src, dst, synth.key_bytes(12, 128), "ctr", bytes(synth.iv_bytes(12)))
+        key, iv = synth.key_bytes(12, 128), bytes(synth.iv_bytes(12))
+        cold = crypt_file(src, dst, key, "ctr", iv)  # pins the chunk buffers (kept for later calls)
+        r = crypt_file(src, dst, key, "ctr", iv)
         r["where"] = base or tempfile.gettempdir()
-        for k in ("seconds", "gbps"):
-            r[k] = round(r[k], 3)
+        r["first_call_gbps"] = round(cold["gbps"], 3)
+        r["first_call_setup_seconds"] = round(cold["setup_seconds"], 4)
+        for k in ("seconds", "gbps", "setup_seconds"):
+            r[k] = round(r[k], 4)
+        r["how"] = ("native aes_file_crypt: worker threads pread chunks into pinned buffers, the kernel "
+                    "encrypts them in place over NVLink-C2C, the chunks are copied into a shared mapping "
+                    "of the output file; second call on the same files (pinned buffers reused)")
         return r
 
 

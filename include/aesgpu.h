@@ -47,7 +47,8 @@ typedef enum aes_status {
     AES_ERR_NOMEM = 7,    /* workspace too small */
     AES_ERR_CUDA = 8,     /* a CUDA call failed; see aes_last_cuda_error() */
     AES_ERR_TIMEOUT = 9,  /* a bounded device wait gave up */
-    AES_ERR_BUSY = 10     /* resource in use */
+    AES_ERR_BUSY = 10,    /* resource in use */
+    AES_ERR_IO = 11       /* a file could not be opened, read or written (aes_file_crypt) */
 } aes_status;
 
 /* Expanded key (FIPS-197 §5.2, paper Fig. 1 step 1).  Plain data, owned by
@@ -243,6 +244,67 @@ aes_status aes_batch_submit_ex(const aes_batch *b, void *d_workspace, size_t wor
  *    stream or synchronise between them. */
 #define AES_BATCH_NOALLOC_MAX_MSGS 65536u
 aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
+
+/* ------------------------------------------------------------------------
+ * File in, encrypted file out: the paper's workload (§IV, Figs. 2-3: a large
+ * file is split into as many chunks as parallel instances, the chunks are
+ * encrypted in parallel and the results concatenated into the output file).
+ *
+ * Here the chunks are fixed-size pieces of the file handed to `threads`
+ * worker threads.  Each worker owns one pinned host buffer and one CUDA
+ * stream and repeats: read its next chunk at the chunk's file offset, run the
+ * cipher on the pinned buffer in place (the kernel reads and writes host
+ * memory over the CPU-GPU link; no device copy), wait for that stream, copy
+ * the chunk to the same offset of dst (through a shared mapping of dst, or
+ * pwrite when dst cannot be mapped).  Reads, writes and GPU work of
+ * different chunks overlap.  Another process truncating dst during the call
+ * makes the mapped copy fault (SIGBUS), as with any mapped file.  CTR chunks use the IV whose 32-bit counter is
+ * advanced by the chunk's first block (mod 2^32), so the output is
+ * byte-identical to one call on the whole file; ECB needs a file length that
+ * is a multiple of 16 (no padding here).
+ *
+ * src_path / dst_path: NUL-terminated paths.  dst is created (mode 0644) or
+ * truncated to the source length; when dst names the same file as src the
+ * file is encrypted in place (each chunk is read before it is rewritten).
+ * ks: expanded key (the caller's, read during the call).  iv: 16 bytes,
+ * CTR only (NULL otherwise).  cfg may be NULL (defaults).  stats may be NULL.
+ * Runs on the calling thread's current CUDA device and returns when dst is
+ * complete (or on the first failure: AES_ERR_IO with stats->os_errno set,
+ * AES_ERR_CUDA, AES_ERR_LENGTH for a ragged ECB file, AES_ERR_ARG for a bad
+ * argument; dst is then incomplete).  Pinned memory: threads buffers of
+ * chunk_bytes rounded up to whole MiB; the call returns them to a
+ * process-wide pool (at most 64 buffers) that later calls reuse, since
+ * pinning host memory costs about as much as a few GB of file traffic;
+ * aes_file_trim() frees the pool. */
+typedef enum aes_file_mode {
+    AES_FILE_CTR = 0,
+    AES_FILE_ECB_ENCRYPT = 1,
+    AES_FILE_ECB_DECRYPT = 2
+} aes_file_mode;
+
+typedef struct aes_file_config {
+    uint64_t chunk_bytes;  /* bytes per chunk: a multiple of 16, 0 = 4 MiB */
+    int32_t threads;       /* worker threads, 1..64; 0 = min(16, hardware threads) */
+    int32_t reserved;      /* 0 */
+} aes_file_config;
+
+typedef struct aes_file_stats {
+    uint64_t bytes;         /* file length */
+    uint64_t chunks;        /* chunks processed */
+    double seconds;         /* wall time of the call */
+    double setup_seconds;   /* of which: pinned buffers and streams */
+    int32_t threads;        /* workers used */
+    int32_t os_errno;       /* errno of the failing file operation (AES_ERR_IO), else 0 */
+} aes_file_stats;
+
+aes_status aes_file_crypt(const char *src_path, const char *dst_path, aes_file_mode mode,
+                          const aes_key_schedule *ks, const uint8_t iv[16],
+                          const aes_file_config *cfg, aes_file_stats *stats);
+
+/* Free the pinned buffers that aes_file_crypt keeps between calls.  Safe at
+ * any time, from any thread; buffers in use by a running call are not in the
+ * pool and stay with that call. */
+void aes_file_trim(void);
 
 /* The CUDA error code behind the calling thread's last AES_ERR_CUDA (0 if none). */
 int aes_last_cuda_error(void);

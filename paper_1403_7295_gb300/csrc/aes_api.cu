@@ -443,6 +443,7 @@ const char* aes_status_string(aes_status s) {
     case AES_ERR_CUDA: return "CUDA error";
     case AES_ERR_TIMEOUT: return "device wait timed out";
     case AES_ERR_BUSY: return "busy";
+    case AES_ERR_IO: return "file open, read or write failed";
   }
   return "unknown status";
 }

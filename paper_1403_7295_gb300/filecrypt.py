@@ -1,141 +1,96 @@
 """Encrypt or decrypt a file on the GPU: the paper's workload (a file in, the
-encrypted file out, §IV) with the chunk split done by a pipeline instead of
-processes.
-
-Three stages overlap through a ring of `depth` pinned buffer pairs:
-
-  reader thread   file -> pinned input buffer (sequential reads)
-  GPU             the library call on the pinned buffers (the kernel reads
-                  and writes host memory over NVLink-C2C; CTR chunks use the
-                  IV advanced by the chunk's first block, so the result is
-                  byte-identical to one call on the whole file)
-  writer thread   pinned output buffer -> file, once the chunk's event fired
-
-ECB needs a file length that is a multiple of 16 (no padding here).
+encrypted file out, §IV), through the library's native pipeline
+``aes_file_crypt`` (include/aesgpu.h): worker threads, each with one pinned
+chunk buffer and one CUDA stream, read a chunk at its file offset, run the
+cipher on the pinned buffer in place (the kernel reads and writes host memory
+over NVLink-C2C), and write the chunk at the same offset of the output.  CTR
+chunks use the IV advanced by the chunk's first block, so the result is
+byte-identical to one call on the whole file.  ECB needs a file length that
+is a multiple of 16 (no padding here).
 
     python -m paper_1403_7295_gb300.filecrypt {ctr,ecb-enc,ecb-dec} SRC DST --key HEX [--iv HEX]
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import os
-import queue
-import threading
-import time
 
 import numpy as np
 
 from . import aes as _aes
-from .shard import ctr_iv_at
+
+MODES = {"ctr": 0, "ecb-enc": 1, "ecb-dec": 2}
 
 
-def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes: int = 64 << 20,
-               depth: int = 3) -> dict:
-    """Process `src` into `dst`; returns bytes, seconds and GB/s (file to file)."""
-    import torch
+class FileConfig(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_uint64), ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
-    if mode not in ("ctr", "ecb-enc", "ecb-dec"):
+
+class FileStats(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("seconds", ctypes.c_double),
+                ("setup_seconds", ctypes.c_double), ("threads", ctypes.c_int32), ("os_errno", ctypes.c_int32)]
+
+
+def _declare():
+    L = _aes.lib()
+    if not getattr(L, "_file_declared", False):
+        L.aes_file_crypt.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
+                                     ctypes.POINTER(_aes.KeySchedule), ctypes.c_void_p,
+                                     ctypes.POINTER(FileConfig), ctypes.POINTER(FileStats)]
+        L.aes_file_crypt.restype = ctypes.c_int
+        L.aes_file_trim.argtypes = []
+        L.aes_file_trim.restype = None
+        L._file_declared = True
+    return L
+
+
+def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes: int = 4 << 20,
+               threads: int = 0) -> dict:
+    """Process `src` into `dst` (the same path encrypts in place); returns
+    bytes, chunks, seconds (of which setup), worker threads and GB/s file to
+    file.  Raises ValueError for a bad mode, IV or ragged ECB length, and
+    OSError / AesError when the native call fails."""
+    if mode not in MODES:
         raise ValueError(f"unknown mode {mode}")
     if chunk_bytes % 16:
         raise ValueError("chunk_bytes must be a multiple of 16")
-    ks = _aes.aes_expand_key(key)
-    size = os.path.getsize(src)
-    if mode != "ctr" and size % 16:
-        raise ValueError("ECB needs a file length that is a multiple of 16")
     if mode == "ctr" and (iv is None or len(bytes(iv)) != 16):
         raise ValueError("CTR needs a 16-byte IV")
-    chunk_bytes = max(16, min(chunk_bytes, (size + 15) // 16 * 16 or 16))
-    bufs_in = [torch.empty(chunk_bytes, dtype=torch.uint8).pin_memory() for _ in range(depth)]
-    bufs_out = [torch.empty(chunk_bytes, dtype=torch.uint8).pin_memory() for _ in range(depth)]
-    free: queue.Queue = queue.Queue()
-    for k in range(depth):
-        free.put(k)
-    filled: queue.Queue = queue.Queue()
-    done: queue.Queue = queue.Queue()
-    errors: list = []
-    stream = torch.cuda.Stream()
+    if mode != "ctr" and os.path.getsize(src) % 16:
+        raise ValueError("ECB needs a file length that is a multiple of 16")
+    ks = _aes.aes_expand_key(key)
+    ivb = ctypes.create_string_buffer(bytes(iv), 16) if mode == "ctr" else None
+    cfg = FileConfig(chunk_bytes, threads, 0)
+    st = FileStats()
+    rc = _declare().aes_file_crypt(os.fsencode(src), os.fsencode(dst), MODES[mode], ctypes.byref(ks),
+                                   ivb, ctypes.byref(cfg), ctypes.byref(st))
+    if rc == 11:  # AES_ERR_IO
+        raise OSError(st.os_errno, os.strerror(st.os_errno) if st.os_errno else "file I/O failed", src)
+    _aes._check(rc, "aes_file_crypt")
+    return {"bytes": st.bytes, "chunks": st.chunks, "seconds": st.seconds, "setup_seconds": st.setup_seconds,
+            "threads": st.threads, "chunk_bytes": chunk_bytes,
+            "gbps": st.bytes / st.seconds / 1e9 if st.seconds > 0 else 0.0}
 
-    def reader():
-        try:
-            with open(src, "rb", buffering=0) as f:
-                off = 0
-                while off < size:
-                    k = free.get()
-                    n = min(chunk_bytes, size - off)
-                    view = memoryview(bufs_in[k].numpy())[:n]
-                    got = 0
-                    while got < n:
-                        r = f.readinto(view[got:])
-                        if not r:
-                            raise IOError("short read")
-                        got += r
-                    filled.put((k, off, n))
-                    off += n
-        except BaseException as e:  # surfaced by the caller
-            errors.append(e)
-        filled.put(None)
 
-    def writer():
-        try:
-            with open(dst, "wb", buffering=0) as f:
-                while True:
-                    item = done.get()
-                    if item is None:
-                        break
-                    k, n, ev = item
-                    ev.synchronize()
-                    mv = memoryview(bufs_out[k].numpy())[:n]
-                    w = 0
-                    while w < n:
-                        w += f.write(mv[w:])
-                    free.put(k)
-        except BaseException as e:
-            errors.append(e)
-            for _ in range(depth):
-                free.put(0)  # unblock the reader
-
-    t0 = time.perf_counter()
-    tr = threading.Thread(target=reader, daemon=True)
-    tw = threading.Thread(target=writer, daemon=True)
-    tr.start()
-    tw.start()
-    while True:
-        item = filled.get()
-        if item is None or errors:
-            break
-        k, off, n = item
-        x, y = bufs_in[k][:n], bufs_out[k][:n]
-        if mode == "ctr":
-            _aes.aes_ctr_xcrypt(ks, ctr_iv_at(iv, off // 16), x, y, stream=stream)
-        elif mode == "ecb-enc":
-            _aes.aes_ecb_encrypt(ks, x, y, stream=stream)
-        else:
-            _aes.aes_ecb_decrypt(ks, x, y, stream=stream)
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        done.put((k, n, ev))
-    done.put(None)
-    tr.join()
-    tw.join()
-    if errors:
-        raise errors[0]
-    dt = time.perf_counter() - t0
-    return {"bytes": size, "seconds": dt, "gbps": size / dt / 1e9 if dt > 0 else 0.0,
-            "chunk_bytes": chunk_bytes, "depth": depth}
+def trim() -> None:
+    """Free the pinned chunk buffers the pipeline keeps between calls."""
+    _declare().aes_file_trim()
 
 
 def main():
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    p.add_argument("mode", choices=["ctr", "ecb-enc", "ecb-dec"])
+    p.add_argument("mode", choices=sorted(MODES))
     p.add_argument("src")
     p.add_argument("dst")
     p.add_argument("--key", required=True, help="hex, 16/24/32 bytes")
     p.add_argument("--iv", default=None, help="hex, 16 bytes (CTR)")
-    p.add_argument("--chunk-mib", type=int, default=64)
+    p.add_argument("--chunk-mib", type=int, default=4)
+    p.add_argument("--threads", type=int, default=0)
     a = p.parse_args()
     iv = bytes.fromhex(a.iv) if a.iv else None
     r = crypt_file(a.src, a.dst, np.frombuffer(bytes.fromhex(a.key), np.uint8), a.mode, iv,
-                   a.chunk_mib << 20)
+                   a.chunk_mib << 20, a.threads)
     print(r)
 
 

@@ -1,6 +1,7 @@
-"""File encryption pipeline: file in, encrypted file out, byte-identical to
-one library call on the whole buffer (and to the oracle), across several
-chunks with a ragged end, for CTR and ECB, and back again."""
+"""File encryption pipeline (aes_file_crypt): file in, encrypted file out,
+byte-identical to one library call on the whole buffer and to the oracle,
+across many chunks with a ragged end, for CTR and ECB, any number of worker
+threads, in place on the same file, and back again."""
 import os
 import tempfile
 
@@ -29,14 +30,50 @@ def test_ctr_file_round_trip(torch, oracle):
     with tempfile.TemporaryDirectory() as d:
         src, enc, dec = (os.path.join(d, f) for f in ("p", "c", "q"))
         data.tofile(src)
-        r = crypt_file(src, enc, key, "ctr", iv, chunk_bytes=4 << 20, depth=3)
-        assert r["bytes"] == n
+        r = crypt_file(src, enc, key, "ctr", iv, chunk_bytes=4 << 20, threads=3)
+        assert r["bytes"] == n and r["chunks"] == 7 and r["threads"] == 3
         got = np.fromfile(enc, np.uint8)
         whole = A.aes_ctr_xcrypt(A.aes_expand_key(key), iv, torch.from_numpy(data).cuda()).cpu().numpy()
         assert np.array_equal(got, whole)
         assert np.array_equal(got[: 1 << 20], oracle.ctr_xcrypt(key, 192, np.frombuffer(iv, np.uint8), data[: 1 << 20]))
-        crypt_file(enc, dec, key, "ctr", iv, chunk_bytes=8 << 20, depth=2)
+        crypt_file(enc, dec, key, "ctr", iv, chunk_bytes=8 << 20, threads=2)
         assert np.array_equal(np.fromfile(dec, np.uint8), data)
+
+
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 1000, 4096 + 3])
+def test_ctr_small_files_tiny_chunks(torch, oracle, n):
+    """Files shorter than a block and chunks of one block: every chunk is its
+    own launch with its own advanced IV."""
+    from paper_1403_7295_gb300.filecrypt import crypt_file
+
+    data = synth.bytes_np(73 + n, synth.STREAM_DATA, n)
+    key = synth.key_bytes(73, 256)
+    iv = synth.iv_bytes(73, counter0=0xFFFFFFFE)
+    want = oracle.ctr_xcrypt(key, 256, iv, data)
+    with tempfile.TemporaryDirectory() as d:
+        src, enc = os.path.join(d, "p"), os.path.join(d, "c")
+        data.tofile(src)
+        for chunk, threads in ((16, 8), (64, 1), (1 << 20, 0)):
+            crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=chunk, threads=threads)
+            assert np.array_equal(np.fromfile(enc, np.uint8), want), (chunk, threads)
+
+
+def test_ctr_in_place_same_file(torch, oracle):
+    from paper_1403_7295_gb300.filecrypt import crypt_file, trim
+
+    n = (3 << 20) + 77
+    data = synth.bytes_np(74, synth.STREAM_DATA, n)
+    key = synth.key_bytes(74, 128)
+    iv = synth.iv_bytes(74)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "f")
+        data.tofile(path)
+        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=1 << 20, threads=4)
+        assert os.path.getsize(path) == n
+        assert np.array_equal(np.fromfile(path, np.uint8), oracle.ctr_xcrypt(key, 128, iv, data))
+        trim()  # the next call pins fresh buffers
+        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=1 << 18, threads=7)
+        assert np.array_equal(np.fromfile(path, np.uint8), data)
 
 
 def test_ecb_file_round_trip(torch, oracle):
@@ -51,7 +88,8 @@ def test_ecb_file_round_trip(torch, oracle):
         crypt_file(src, enc, key, "ecb-enc", chunk_bytes=5 << 20)
         got = np.fromfile(enc, np.uint8)
         assert np.array_equal(got[: 1 << 16], oracle.ecb_encrypt(key, 128, data[: 1 << 16]))
-        crypt_file(enc, dec, key, "ecb-dec", chunk_bytes=3 << 20)
+        assert np.array_equal(got[-(1 << 16):], oracle.ecb_encrypt(key, 128, data[-(1 << 16):]))
+        crypt_file(enc, dec, key, "ecb-dec", chunk_bytes=3 << 20, threads=5)
         assert np.array_equal(np.fromfile(dec, np.uint8), data)
         open(src, "ab").write(b"x")
         with pytest.raises(ValueError):

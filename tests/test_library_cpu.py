@@ -117,7 +117,7 @@ def test_validation_before_any_cuda_call(lib):
 
 
 def test_status_strings(lib):
-    for s in range(11):
+    for s in range(12):
         assert lib.aes_status_string(s)
     assert lib.aes_status_string(99) == b"unknown status"
 
@@ -137,3 +137,37 @@ def test_cbc_and_xts_validation(lib):
         assert fn(kr, None, 0, 512, base, base, 512, None) == 1
         assert fn(kr, kr, 0, 512, base + 8, base + 8, 512, None) == 4        # misaligned
         assert fn(kr, kr, 0, 512, base, base, 0, None) == 0
+
+
+def test_file_crypt_validation_and_empty_file(lib, tmp_path):
+    """aes_file_crypt: argument checks, a missing source (AES_ERR_IO with
+    errno), a ragged ECB file (AES_ERR_LENGTH before dst is created), and an
+    empty file (done without a GPU: dst created empty)."""
+    import errno
+
+    from paper_1403_7295_gb300 import filecrypt as F
+
+    L = F._declare()
+    ks = A.aes_expand_key(synth.key_bytes(0, 128))
+    kr = ctypes.byref(ks)
+    ivb = ctypes.create_string_buffer(16)
+    src, dst = tmp_path / "src", tmp_path / "dst"
+    src.write_bytes(b"")
+    s, d = os.fsencode(src), os.fsencode(dst)
+    st = F.FileStats()
+    assert L.aes_file_crypt(None, d, 0, kr, ivb, None, None) == 1
+    assert L.aes_file_crypt(s, d, 3, kr, ivb, None, None) == 1                     # unknown mode
+    assert L.aes_file_crypt(s, d, 0, kr, None, None, None) == 1                    # CTR without IV
+    assert L.aes_file_crypt(s, d, 0, None, ivb, None, None) == 1                   # no key
+    for cfg in (F.FileConfig(17, 0, 0), F.FileConfig(0, 65, 0), F.FileConfig(0, -1, 0), F.FileConfig(0, 0, 1)):
+        assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(cfg), None) == 1
+    missing = os.fsencode(tmp_path / "missing")
+    assert L.aes_file_crypt(missing, d, 0, kr, ivb, None, ctypes.byref(st)) == 11
+    assert st.os_errno == errno.ENOENT
+    src.write_bytes(b"x" * 33)
+    assert L.aes_file_crypt(s, d, 1, kr, None, None, None) == 3                    # ECB of 33 bytes
+    assert not dst.exists()
+    src.write_bytes(b"")
+    assert L.aes_file_crypt(s, d, 0, kr, ivb, None, ctypes.byref(st)) == 0
+    assert dst.exists() and dst.stat().st_size == 0 and st.bytes == 0 and st.chunks == 0
+    L.aes_file_trim()  # nothing pinned yet: a no-op without a GPU
