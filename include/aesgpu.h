@@ -195,8 +195,12 @@ typedef struct aes_batch {
 
 /* Optional launch shape of the persistent kernel; zero fields = default. */
 typedef struct aes_batch_config {
-    int32_t cta_threads;  /* 256..1024, multiple of 32 */
-    int32_t tile_blocks;  /* 16-byte blocks a CTA claims at a time: multiple of cta_threads, <= 65536 */
+    int32_t cta_threads;  /* 256..1024, multiple of 32; up to 512 selects the build with 128
+                             registers per thread, which keeps a long message's round keys in
+                             registers across a span */
+    int32_t tile_blocks;  /* 16-byte blocks a CTA claims at a time: multiple of cta_threads, <= 2^20;
+                             0 = sized from the batch: ~4 tiles per CTA of the long messages' blocks,
+                             at most 65536 */
     int32_t grid_ctas;    /* 0 = one per SM */
     int32_t reserved;
 } aes_batch_config;

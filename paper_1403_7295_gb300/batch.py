@@ -192,8 +192,8 @@ class Batch:
 # autotuner: launch shapes of the persistent kernel, timed on the batch itself
 # ---------------------------------------------------------------------------
 
-CANDIDATES = [(cta, tile) for cta in (512, 1024) for tile in (2048, 4096, 8192, 16384, 32768)
-              if tile % cta == 0]
+CANDIDATES = [(cta, tile) for cta in (512, 1024) for tile in (0, 8192, 16384, 32768, 65536, 131072)
+              if tile % cta == 0]  # tile 0: sized by the kernel from the batch
 _CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "batch_tune.json")
 
 

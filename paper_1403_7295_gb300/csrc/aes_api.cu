@@ -285,10 +285,10 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
   if (b->iv && !aligned(b->iv, 16)) return AES_ERR_ALIGN;
   if (ws_bytes < batch_workspace_bytes(b->n_msgs)) return AES_ERR_NOMEM;
   int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : 1024;
-  int tile = (cfg && cfg->tile_blocks) ? cfg->tile_blocks : 8192;
+  int tile = (cfg && cfg->tile_blocks) ? cfg->tile_blocks : 0;  // 0: sized by the kernel
   int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
   if (cta < 256 || cta > 1024 || cta % 32) return AES_ERR_ARG;
-  if (tile < cta || tile > 65536 || tile % cta) return AES_ERR_ARG;
+  if (tile != 0 && (tile < cta || tile > (1 << 20) || tile % cta)) return AES_ERR_ARG;
   if (grid < 1) return AES_ERR_ARG;
   const void* din = nullptr;
   void* dout = nullptr;

@@ -635,12 +635,79 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
   }
 }
 
+// Round-key source of the span loop: shared memory (one 128-bit broadcast
+// load per round), or registers loaded once per span (kRegKeys: 512-thread
+// CTAs, whose 128 registers per thread hold a whole schedule).
+template <int NR, bool kRegKeys, int kFirstWord>
+struct SpanKeys {
+  uint32_t w[kRegKeys ? 4 * (NR + 1) - kFirstWord : 1];
+  const uint32_t* rk;
+  __device__ __forceinline__ explicit SpanKeys(const uint32_t* src) : rk(src) {
+    if (kRegKeys) {
+#pragma unroll
+      for (int i = kFirstWord; i < 4 * (NR + 1); i += 4) {
+        const uint4 k = lds128(src + i);
+        w[i - kFirstWord] = k.x;
+        w[i - kFirstWord + 1] = k.y;
+        w[i - kFirstWord + 2] = k.z;
+        w[i - kFirstWord + 3] = k.w;
+      }
+    }
+  }
+  // words 4r .. 4r+3
+  __device__ __forceinline__ void round(int r, uint32_t kk[4]) const {
+    if (kRegKeys) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) kk[j] = w[4 * r - kFirstWord + j];
+    } else {
+      const uint4 k = lds128(rk + 4 * r);
+      kk[0] = k.x;
+      kk[1] = k.y;
+      kk[2] = k.z;
+      kk[3] = k.w;
+    }
+  }
+};
+
+template <int NR, bool kRegKeys, int kFirstWord>
+__device__ __forceinline__ State enc_rounds_keys(const Tabs& T, State s, const SpanKeys<NR, kRegKeys, kFirstWord>& K,
+                                                 int first) {
+#pragma unroll
+  for (int r = 1; r < NR; ++r) {
+    if (r < first) continue;
+    uint32_t kk[4];
+    K.round(r, kk);
+    enc_round(T, s, kk);
+  }
+  uint32_t kk[4];
+  K.round(NR, kk);
+  enc_final(T, s, kk);
+  return s;
+}
+
+template <int NR, bool kRegKeys>
+__device__ __forceinline__ State dec_rounds_keys(const Tabs& T, State s, const SpanKeys<NR, kRegKeys, 0>& K) {
+#pragma unroll
+  for (int r = 1; r < NR; ++r) {
+    uint32_t kk[4];
+    K.round(r, kk);
+    dec_round(T, s, kk);
+  }
+  uint32_t kk[4];
+  K.round(NR, kk);
+  dec_final(T, s, kk);
+  return s;
+}
+
 // A whole span (256 blocks) inside one message, every block whole: the same
 // work as process_block with the round count fixed and no per-block checks.
-template <int OPB, int NR>
+template <int OPB, int NR, bool kRegKeys>
 __device__ __forceinline__ void span_fast(const BatchArgs& a, const Tabs& T, const Slot* slots,
                                           const uint32_t* rk, const Cur& c, uint32_t span,
                                           uint32_t lane, RunCache& rc) {
+  // CTR's rounds 1-2 come from the run cache: its loop reads keys from round 3
+  constexpr int kFirstWord = OPB == kBatchCtr ? 12 : 0;
+  const SpanKeys<NR, kRegKeys, kFirstWord> K(rk);
   const uint4* src = reinterpret_cast<const uint4*>(c.src) + span + lane;
   uint4* dst = reinterpret_cast<uint4*>(c.dst) + span + lane;
   uint4 v = __ldcs(src);
@@ -649,7 +716,7 @@ __device__ __forceinline__ void span_fast(const BatchArgs& a, const Tabs& T, con
     uint4 vn = v;
     if (k < 7) vn = __ldcs(src + 32 * (k + 1));
     State s;
-    if (OPB == kBatchCtr) {
+    if constexpr (OPB == kBatchCtr) {
       const uint32_t ctr = c.ctr + span + 32 * k + lane;
       if ((ctr >> 8) != rc.run || c.slot + 1 != rc.slot) {
         rc.run = ctr >> 8;
@@ -666,17 +733,19 @@ __device__ __forceinline__ void span_fast(const BatchArgs& a, const Tabs& T, con
       }
       const uint32_t s0 = rc.c10 ^ T.t3(rc.xr ^ ((ctr & 255u) << 24));
       s = State{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
-      s = enc_rounds_smem<NR>(T, s, rk, 3);
+      s = enc_rounds_keys<NR>(T, s, K, 3);
       __stcs(dst + 32 * k, make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3));
-    } else if (OPB == kBatchEcbEnc) {
-      const uint4 k0 = lds128(rk);
-      s = State{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-      s = enc_rounds_smem<NR>(T, s, rk, 1);
+    } else if constexpr (OPB == kBatchEcbEnc) {
+      uint32_t k0[4];
+      K.round(0, k0);
+      s = State{v.x ^ k0[0], v.y ^ k0[1], v.z ^ k0[2], v.w ^ k0[3]};
+      s = enc_rounds_keys<NR>(T, s, K, 1);
       __stcs(dst + 32 * k, make_uint4(s.s0, s.s1, s.s2, s.s3));
     } else {
-      const uint4 k0 = lds128(rk);
-      s = State{v.x ^ k0.x, v.y ^ k0.y, v.z ^ k0.z, v.w ^ k0.w};
-      s = dec_rounds_smem<NR>(T, s, rk);
+      uint32_t k0[4];
+      K.round(0, k0);
+      s = State{v.x ^ k0[0], v.y ^ k0[1], v.z ^ k0[2], v.w ^ k0[3]};
+      s = dec_rounds_keys<NR>(T, s, K);
       __stcs(dst + 32 * k, make_uint4(s.s0, s.s1, s.s2, s.s3));
       const uint32_t gr = span + 32 * k + lane;
       if (((c.nr >> 16) & 1u) && gr + 1 == c.e) {  // the message's last block: check PKCS#7
@@ -714,19 +783,30 @@ __device__ __forceinline__ void run_blocks(const BatchArgs& a, const Tabs& T, co
   }
 }
 
+// Tile size when the caller gives none: about 4 tiles per CTA of the
+// long-message blocks (so CTAs finish close together while each tile's
+// serial part, the claim, window load and barriers, stays small against
+// its blocks), a whole number of CTA widths, at most 65536 blocks (measured
+// best for large batches).
+__device__ __forceinline__ uint32_t auto_tile(uint64_t total, uint32_t ctas, uint32_t cta_threads) {
+  uint64_t t = (total + 4ull * ctas - 1) / (4ull * ctas);
+  t = (t + cta_threads - 1) / cta_threads * cta_threads;
+  return static_cast<uint32_t>(t < cta_threads ? cta_threads : t > 65536 ? 65536 : t);
+}
+
 // Warp 0: claim the next tile and find its first and last message.
-__device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total,
+__device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total, uint32_t tile,
                                            unsigned long long* s_tile, uint32_t* s_mlo,
                                            uint32_t* s_mhi) {
   const uint32_t lane = threadIdx.x & 31;
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(a.tile_counter, 1ull);
   t = __shfl_sync(0xffffffffu, t, 0);
-  const uint64_t t0 = t * a.tile_blocks;
+  const uint64_t t0 = t * tile;
   uint32_t mlo = 0, mhi = 0;
   if (t0 < total) {
     mlo = warp_find(a.blk_off, a.n, t0);
-    mhi = warp_find(a.blk_off, a.n, min(t0 + a.tile_blocks, total) - 1);
+    mhi = warp_find(a.blk_off, a.n, min(t0 + tile, total) - 1);
   }
   if (lane == 0) {
     *s_tile = t;
@@ -951,8 +1031,10 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
   }
 }
 
-template <int OPB>
-__global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
+// kRegKeys: the 512-thread build (128 registers per thread), whose span loop
+// keeps the message's round keys in registers.
+template <int OPB, bool kRegKeys>
+__global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
   constexpr int kWin = WindowSize<OPB>::value;
   constexpr bool kDec = OPB == kBatchEcbDec;
   extern __shared__ __align__(16) uint32_t smem[];
@@ -964,7 +1046,8 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.blk_off[a.n];
-  if (warp == 0) claim_tile(a, total, &s_tile[0], &s_mlo[0], &s_mhi[0]);  // overlaps the table fill
+  const uint32_t tile = a.tile_blocks ? a.tile_blocks : auto_tile(total, gridDim.x, blockDim.x);
+  if (warp == 0) claim_tile(a, total, tile, &s_tile[0], &s_mlo[0], &s_mhi[0]);  // overlaps the table fill
 
   fill_tables<kDec>(smem);
   if (kDec) {  // forward S-box (all four bytes) beside the inverse one, for key expansion
@@ -987,10 +1070,10 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
   for (uint32_t it = 0;; ++it) {
     __syncthreads();  // tile `it` is visible (and, first time, the tables)
     const uint32_t cur = it & 1;
-    const uint64_t t0 = s_tile[cur] * a.tile_blocks;
+    const uint64_t t0 = s_tile[cur] * tile;
     const uint32_t m_lo = s_mlo[cur], m_hi = s_mhi[cur];
     if (t0 >= total) break;
-    const uint64_t t1 = min(t0 + a.tile_blocks, total);
+    const uint64_t t1 = min(t0 + tile, total);
     for (uint32_t w0 = m_lo; w0 <= m_hi; w0 += kWin) {
       const uint32_t wn = min(static_cast<uint32_t>(kWin), m_hi - w0 + 1);
       for (uint32_t sl = first_slot; sl < wn; sl += blockDim.x)
@@ -1001,7 +1084,7 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
       // it + 1 into the other entry (last read before this tile's barrier)
       // and joins the spans afterwards.
       if (w0 == m_lo && warp == 0)
-        claim_tile(a, total, &s_tile[cur ^ 1], &s_mlo[cur ^ 1], &s_mhi[cur ^ 1]);
+        claim_tile(a, total, tile, &s_tile[cur ^ 1], &s_mlo[cur ^ 1], &s_mhi[cur ^ 1]);
       const uint32_t gr0 = static_cast<uint32_t>(max(t0, slots[0].blk_start) - t0);
       const uint32_t gr1 = static_cast<uint32_t>(min(t1, slots[wn - 1].blk_end) - t0);
       Cur c{1, 0, 0, 0, 0, 0, 0, 0};  // empty: the first block selects its message
@@ -1024,9 +1107,9 @@ __global__ void __launch_bounds__(1024, 1) batch_kernel(const __grid_constant__ 
           if (whole) {
             const uint32_t* rk = rk_all + c.slot * kRkStride;
             switch (c.nr & 0xFFu) {
-              case 10: span_fast<OPB, 10>(a, T, slots, rk, c, span, lane, rc); break;
-              case 12: span_fast<OPB, 12>(a, T, slots, rk, c, span, lane, rc); break;
-              default: span_fast<OPB, 14>(a, T, slots, rk, c, span, lane, rc); break;
+              case 10: span_fast<OPB, 10, kRegKeys>(a, T, slots, rk, c, span, lane, rc); break;
+              case 12: span_fast<OPB, 12, kRegKeys>(a, T, slots, rk, c, span, lane, rc); break;
+              default: span_fast<OPB, 14, kRegKeys>(a, T, slots, rk, c, span, lane, rc); break;
             }
             continue;
           }
@@ -1044,7 +1127,7 @@ template <int OPB>
 cudaError_t launch_persistent(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
   constexpr size_t smem = batch_smem_bytes<OPB>();
   static_assert(smem + 64 <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
-  auto kern = batch_kernel<OPB>;
+  auto kern = cta <= 512 ? batch_kernel<OPB, true> : batch_kernel<OPB, false>;
   cudaError_t e = ensure_dynamic_smem(kern, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<grid, cta, smem, s>>>(a);
