@@ -557,8 +557,10 @@ def batched_arm(torch, A, ctr128_gbps):
     gbps = nbytes * steps / (ms / 1e3) / 1e9
     by_bits = {bits: float(lengths[kb == bits].sum()) for bits in (128, 192, 256)}
     mix = sum(by_bits.values()) / sum(by_bits[k] / rates[k] for k in by_bits)
+    st = per_step_stats(torch, b.replay, 20)
     out["varlen_16384"] = {
         "gbps": round(gbps, 1), "bytes": nbytes, "ms_per_batch": round(ms / steps, 3),
+        "per_batch": {k: st[k] for k in ("median_ms", "p99_ms", "paper_mean_ms")},
         "plain_ctr_1GiB_gbps": {str(k): round(v, 1) for k, v in rates.items()},
         "plain_mix_gbps": round(mix, 1), "ratio_vs_plain": round(gbps / mix, 4),
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
@@ -605,6 +607,7 @@ def batched_arm(torch, A, ctr128_gbps):
     cfg = B.autotune(b)
     b.capture(cfg)
     ms_dev = time_graph(torch, b, steps)
+    st_small = per_step_stats(torch, b.replay, 30)
     nbytes = b.total_input_bytes()
     # the same batch with pre-expanded schedules (one per message)
     table = bytearray()
@@ -621,6 +624,7 @@ def batched_arm(torch, A, ctr128_gbps):
         "gbps_preexpanded": round(nbytes * steps / (ms_pre / 1e3) / 1e9, 1),
         "bytes": nbytes, "ms_per_batch_device_keys": round(ms_dev / steps, 3),
         "ms_per_batch_preexpanded": round(ms_pre / steps, 3),
+        "per_batch_device_keys": {k: st_small[k] for k in ("median_ms", "p99_ms", "paper_mean_ms")},
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
     }
     return out
@@ -726,15 +730,19 @@ def sweep(torch, A):
         n = size_mib << 20
         x = synth.bytes_torch(100 + size_mib, synth.STREAM_DATA, n, device="cuda")
         y = torch.empty_like(x)
-        steps = max(5, int(2 * 2**30 / n * 10))
+        steps = max(20, int(2 * 2**30 / n * 10))
         for bits in (128, 192, 256):
             for mode in ("ecb_enc", "ecb_dec", "ctr_enc", "ctr_dec"):
                 ks = A.aes_expand_key(synth.key_bytes(run, bits))
                 iv = synth.iv_bytes(run)
                 m = "ctr" if mode.startswith("ctr") else mode
-                ms = time_device(torch, lambda: launch(A, m, ks, iv, x, y, None), steps, 3)
+                fn = lambda: launch(A, m, ks, iv, x, y, None)  # noqa: E731
+                ms = time_device(torch, fn, steps, 3)
+                st = per_step_stats(torch, fn, min(steps, 50))
                 out.append({"bits": bits, "mode": mode, "size_mib": size_mib,
-                            "gbps": round(n * steps / (ms / 1e3) / 1e9, 1)})
+                            "gbps": round(n * steps / (ms / 1e3) / 1e9, 1),
+                            "median_ms": st["median_ms"], "p99_ms": st["p99_ms"],
+                            "paper_mean_ms": st["paper_mean_ms"]})
                 run += 1
         del x, y
         torch.cuda.empty_cache()

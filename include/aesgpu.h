@@ -171,6 +171,14 @@ typedef enum aes_batch_op {
 /* Description of one batch.  The struct itself is read on the host during
  * the call; every array it points to is device memory, owned by the caller,
  * and must stay valid until the stream has executed the work. */
+/* aes_batch.flags: promises that let the kernel treat a message's last,
+ * ragged block as a whole 16-byte block (one vector load / store instead of
+ * byte-exact ones).  Offsets are multiples of 16, so the bytes concerned lie
+ * between a message's end and the next 16-byte boundary. */
+#define AES_BATCH_IN_PADDED 1u  /* each input may be read up to the next 16-byte boundary */
+#define AES_BATCH_OUT_PADDED 2u /* output bytes up to the next 16-byte boundary after each message's
+                                   output may be overwritten (their values are unspecified) */
+
 typedef struct aes_batch {
     uint32_t n_msgs;
     uint32_t op;                  /* aes_batch_op */
@@ -187,7 +195,8 @@ typedef struct aes_batch {
     const aes_key_schedule *schedules; /* [n_schedules] device table (when keys == NULL) */
     const uint32_t *sched_idx;    /* [n_msgs] index into schedules */
     uint32_t n_schedules;
-    uint32_t reserved;
+    uint32_t flags;               /* 0 (every read and write exact to the byte), or
+                                     AES_BATCH_IN_PADDED | AES_BATCH_OUT_PADDED */
     const uint8_t *iv;            /* [n_msgs][16] IVs, 16-B aligned (CTR only; else NULL) */
     uint64_t *out_len;            /* [n_msgs] out: output bytes per message (may be NULL) */
     int32_t *status;              /* [n_msgs] out: aes_status per message (may be NULL) */
@@ -215,7 +224,7 @@ size_t aes_batch_workspace_size(uint32_t n_msgs);
  * contents need no initialisation.  Per-message failures (bad key size,
  * unaligned offset, bad ECB length or padding) are reported in status[m]
  * with zero output bytes; the rest of the batch proceeds.  Returns
- * AES_ERR_ARG for missing arrays or an unknown op, AES_ERR_NOMEM for a
+ * AES_ERR_ARG for missing arrays, an unknown op or unknown flags, AES_ERR_NOMEM for a
  * short workspace, AES_ERR_ALIGN for a misaligned arena, key or IV base.
  * Messages are not checked against each other for overlap. */
 aes_status aes_batch_submit(const aes_batch *b, void *d_workspace, size_t workspace_bytes,

@@ -20,6 +20,8 @@ from . import aes as _aes
 BATCH_CTR = 0
 BATCH_ECB_PKCS7_ENCRYPT = 1
 BATCH_ECB_PKCS7_DECRYPT = 2
+IN_PADDED = 1   # AES_BATCH_IN_PADDED
+OUT_PADDED = 2  # AES_BATCH_OUT_PADDED
 
 
 class AesBatch(ctypes.Structure):
@@ -30,7 +32,7 @@ class AesBatch(ctypes.Structure):
         ("in_off", ctypes.c_void_p), ("in_len", ctypes.c_void_p), ("out_off", ctypes.c_void_p),
         ("keys", ctypes.c_void_p), ("key_bits", ctypes.c_void_p),
         ("schedules", ctypes.c_void_p), ("sched_idx", ctypes.c_void_p),
-        ("n_schedules", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("n_schedules", ctypes.c_uint32), ("flags", ctypes.c_uint32),
         ("iv", ctypes.c_void_p), ("out_len", ctypes.c_void_p), ("status", ctypes.c_void_p),
     ]
 
@@ -99,11 +101,17 @@ class Batch:
     indices into a device table of ``aes_key_schedule`` (``schedules`` +
     ``sched_idx``); ``ivs`` [n,16] for CTR.  The output arena is allocated
     here unless ``out`` is given.
+
+    ``padded``: None (default) sets ``AES_BATCH_IN_PADDED`` when ``data``
+    holds every message up to its next 16-byte boundary, and
+    ``AES_BATCH_OUT_PADDED`` when the output arena is allocated here (its
+    gaps belong to no one); False keeps every read and write exact to the
+    byte; True asserts both for caller-given arenas.
     """
 
     def __init__(self, op: int, data, in_off, lengths, *, keys=None, key_bits=None,
                  schedules=None, n_schedules: int = 0, sched_idx=None, ivs=None, out=None,
-                 out_off=None, device="cuda"):
+                 out_off=None, device="cuda", padded: bool | None = None):
         import torch
 
         self.op = op
@@ -141,6 +149,13 @@ class Batch:
         self.out_len = torch.zeros(max(self.n, 1), dtype=torch.int64, device=dev)
         self.status = torch.zeros(max(self.n, 1), dtype=torch.int32, device=dev)
         self.workspace = torch.empty(aes_batch_workspace_size(self.n), dtype=torch.uint8, device=dev)
+        if padded is None:
+            in_off_np = np.asarray(in_off, dtype=np.uint64)
+            ends = (in_off_np + self.lengths_np + np.uint64(15)) // np.uint64(16) * np.uint64(16)
+            fits = self.n == 0 or int(ends.max()) <= data.numel() * data.element_size()
+            self.flags = (IN_PADDED if fits else 0) | (OUT_PADDED if out is None else 0)
+        else:
+            self.flags = IN_PADDED | OUT_PADDED if padded else 0
         self.desc = self._descriptor()
         self.graph = None
 
@@ -156,6 +171,7 @@ class Batch:
         d.schedules = p(self.schedules)
         d.sched_idx = p(self.sched_idx)
         d.n_schedules = self.n_schedules
+        d.flags = self.flags
         d.iv = p(self.ivs)
         d.out_len, d.status = p(self.out_len), p(self.status)
         return d

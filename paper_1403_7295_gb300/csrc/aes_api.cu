@@ -271,6 +271,7 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
                         const aes_batch_config* cfg) {
   if (b == nullptr) return AES_ERR_ARG;
   if (b->op > AES_BATCH_ECB_PKCS7_DECRYPT) return AES_ERR_ARG;
+  if (b->flags & ~(AES_BATCH_IN_PADDED | AES_BATCH_OUT_PADDED)) return AES_ERR_ARG;
   if (b->n_msgs == 0) return AES_OK;
   if (!b->in || !b->out || !b->in_off || !b->in_len || !b->out_off) return AES_ERR_ARG;
   const bool raw_keys = b->keys != nullptr;
@@ -312,6 +313,7 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
   a.sched_idx = raw_keys ? nullptr : b->sched_idx;
   a.n_sched = raw_keys ? 0 : b->n_schedules;
   a.tile_blocks = static_cast<uint32_t>(tile);
+  a.flags = b->flags;
   a.iv = b->iv;
   a.out_len = b->out_len;
   a.status = b->status;

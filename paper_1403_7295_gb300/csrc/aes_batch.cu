@@ -548,9 +548,12 @@ __device__ __forceinline__ void store_partial(uint8_t* p, const uint4& v, uint32
 
 // Input of tile block gr of the current message: a whole block, or the
 // leading `rem` bytes of the last one (zero above).
+// (With AES_BATCH_IN_PADDED the last block is read whole; the bytes past the
+// message are the caller's padding.)
 template <int OPB>
-__device__ __forceinline__ uint4 load_block(const Cur& c, uint32_t gr) {
-  if (OPB == kBatchEcbDec || gr < c.f) return __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
+__device__ __forceinline__ uint4 load_block(const BatchArgs& a, const Cur& c, uint32_t gr) {
+  if (OPB == kBatchEcbDec || gr < c.f || (a.flags & AES_BATCH_IN_PADDED))
+    return __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
   return load_partial(reinterpret_cast<const uint8_t*>(c.src + 16ull * gr), (c.nr >> 8) & 0xFFu);
 }
 
@@ -596,7 +599,7 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
     s = State{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
     s = enc_any(T, s, rk, nr, 3);
     }
-    if (full) {
+    if (full || (a.flags & AES_BATCH_OUT_PADDED)) {
       __stcs(reinterpret_cast<uint4*>(dst),
              make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3));
     } else {  // partial last block (v_in holds its `rem` bytes): the leading `rem` bytes
@@ -775,10 +778,10 @@ __device__ __forceinline__ void run_blocks(const BatchArgs& a, const Tabs& T, co
   for (uint32_t gr = g_begin + lane; gr < g_end; gr += 32) {
     if (gr < c.s || gr >= c.e) select_message(slots, wn, t0, t1, gr, c);
     uint4 v = next;
-    if (!have_next) v = load_block<OPB>(c, gr);
+    if (!have_next) v = load_block<OPB>(a, c, gr);
     const uint32_t gn = gr + 32;
     have_next = gn < g_end && gn < c.e;
-    if (have_next) next = load_block<OPB>(c, gn);
+    if (have_next) next = load_block<OPB>(a, c, gn);
     process_block<OPB>(a, T, slots, rk_all + c.slot * kRkStride, c, gr, v, rc);
   }
 }
@@ -863,7 +866,7 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
   const uint8_t* src = reinterpret_cast<const uint8_t*>(r.src0 + 16ull * gr);
   uint8_t* dst = reinterpret_cast<uint8_t*>(r.dst0 + 16ull * gr);
   uint4 v;
-  if (OPB == kBatchEcbDec || full) v = __ldcs(reinterpret_cast<const uint4*>(src));
+  if (OPB == kBatchEcbDec || full || (a.flags & AES_BATCH_IN_PADDED)) v = __ldcs(reinterpret_cast<const uint4*>(src));
   else v = load_partial(src, rem);
   if (OPB == kBatchCtr) {
     const uint32_t ctr = r.ctr0 + gr;
@@ -882,7 +885,7 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
     State s{d.x ^ T.t0(s0), d.y ^ T.t3(s0), d.z ^ T.t2(s0), d.w ^ T.t1(s0)};
     s = enc_lanes(T, s, rk, nr, 3);
     const uint4 o = make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3);
-    if (full) __stcs(reinterpret_cast<uint4*>(dst), o);
+    if (full || (a.flags & AES_BATCH_OUT_PADDED)) __stcs(reinterpret_cast<uint4*>(dst), o);
     else store_partial(dst, o, rem);
   } else if (OPB == kBatchEcbEnc) {
     if (!full) {  // last block: rem message bytes then PKCS#7 pad bytes of value 16 - rem

@@ -26,6 +26,7 @@ struct BatchArgs {
   const uint32_t* sched_idx;
   uint32_t n_sched;
   uint32_t tile_blocks;
+  uint32_t flags;  // AES_BATCH_IN_PADDED | AES_BATCH_OUT_PADDED
   const uint8_t* iv;
   uint64_t* out_len;
   int32_t* status;

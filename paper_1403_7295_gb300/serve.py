@@ -238,6 +238,11 @@ class Server:
             d.schedules = self.schedules.data_ptr()
             d.sched_idx = slot.dptr("sched_idx")
             d.n_schedules = self.n_tenants
+            # outputs sit in 16-byte-rounded ring allocations; inputs may be read
+            # to their next 16-byte boundary when the pool holds it
+            pool_bytes = self.pool.numel()
+            d.flags = _batch.OUT_PADDED | (_batch.IN_PADDED if all(
+                (r.in_off + r.length + 15) // 16 * 16 <= pool_bytes for r in reqs) else 0)
             d.iv = slot.dptr("iv")
             d.out_len, d.status = slot.dptr("out_len"), slot.dptr("status")
             cfg = _batch.AesBatchConfig(0, 0, self.grid, 0) if self.grid else None

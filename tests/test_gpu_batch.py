@@ -105,7 +105,8 @@ def test_batch_writes_nothing_outside_messages(torch, B, oracle, op):
     kb = W.key_sizes(31, n)
     keys = W.message_keys(31, n)
     ivs = W.message_ivs(31, n)
-    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=32)
+    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=32, padded=False)
+    assert b.flags == 0
     b.out.fill_(0xA5)
     b.submit()
     torch.cuda.synchronize()
@@ -117,6 +118,27 @@ def test_batch_writes_nothing_outside_messages(torch, B, oracle, op):
         o = int(b.out_off_np[m])
         written[o: o + int(ol[m])] = True
     assert np.all(out[~written] == 0xA5)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("padded", [False, True])
+def test_batch_exact_and_padded_last_blocks(torch, B, oracle, op, padded):
+    """The ragged last block read and written byte-exactly (flags 0) or as a
+    whole block (AES_BATCH_IN_PADDED | AES_BATCH_OUT_PADDED): identical
+    message bytes, short and long messages, every key size."""
+    n = 500
+    lengths = mixed_lengths(35 + op, n)
+    kb = W.key_sizes(35, n)
+    keys = W.message_keys(35, n)
+    ivs = W.message_ivs(35, n, counter0=0xFFFFFF00)
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(36, synth.STREAM_DATA, total, device="cuda")  # exactly the packed size
+    b = B.Batch(op, data, in_off, lengths, keys=keys, key_bits=kb, ivs=ivs if op == 0 else None,
+                padded=None if padded else False)
+    assert b.flags == (3 if padded else 0)
+    b.submit()
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, b, kb, keys, ivs)
 
 
 def test_batch_decrypt_round_trip_and_bad_padding(torch, B, oracle):
@@ -296,6 +318,9 @@ def test_batch_host_validation(torch, B):
     cfg = B.AesBatchConfig(1024, 1000, 0, 0)  # tile not a multiple of the CTA
     with pytest.raises(A.AesError):
         b.submit(config=cfg)
+    d = B.AesBatch.from_buffer_copy(b.desc)
+    d.flags = 4  # unknown flag bit
+    assert L.aes_batch_submit(ctypes.byref(d), ws.data_ptr(), ws.numel(), None) == 1
     d = B.AesBatch.from_buffer_copy(b.desc)
     d.n_msgs = 0
     assert L.aes_batch_submit(ctypes.byref(d), None, 0, None) == 0
