@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(1024, 1)
     cbc_decrypt_kernel(const uint4* in, uint4* out, uint64_t nblocks,
                        const __grid_constant__ RoundKeys rk, const __grid_constant__ CtrParams cp) {
   extern __shared__ __align__(16) uint32_t smem[];
+  pdl_launch_dependents();
   fill_tables<true>(smem);
   __syncthreads();
+  pdl_wait_previous();  // the caller's buffers are touched only after this point
   const uint32_t lane = threadIdx.x & 31;
   const char* base = reinterpret_cast<const char*>(smem);
   const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
@@ -125,12 +127,14 @@ __global__ void __launch_bounds__(1024, 1)
     xts_kernel(const uint4* in, uint4* out, uint64_t nblocks, const __grid_constant__ RoundKeys rk1,
                const __grid_constant__ RoundKeys rk2, const __grid_constant__ XtsParams xp) {
   extern __shared__ __align__(16) uint32_t smem[];
+  pdl_launch_dependents();
   fill_tables<kDec>(smem);
   if (kDec) {  // te0 replicas in the upper half of each inverse S-box row, for the tweak cipher
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int x = warp; x < 256; x += nwarps) smem[kRegionC / 4 + x * 64 + 32 + lane] = kDevTables.te0[x];
   }
   __syncthreads();
+  pdl_wait_previous();  // the caller's buffers are touched only after this point
   const uint32_t lane = threadIdx.x & 31;
   const char* base = reinterpret_cast<const char*>(smem);
   const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
@@ -189,9 +193,8 @@ cudaError_t launch_cbc(const void* in, void* out, uint64_t nblocks, const RoundK
   if (e != cudaSuccess) return e;
   const uint64_t needed = (nblocks + shape.cta_threads - 1) / shape.cta_threads;
   const uint64_t grid = shape.grid_ctas < needed ? shape.grid_ctas : (needed ? needed : 1);
-  kern<<<static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemDec, stream>>>(
-      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk, cp);
-  return cudaGetLastError();
+  return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemDec, stream,
+                    static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk, cp);
 }
 
 template <bool kDec, int NR>
@@ -206,9 +209,8 @@ cudaError_t launch_xts(const void* in, void* out, uint64_t nblocks, const RoundK
   const uint64_t warps_per_cta = shape.cta_threads / 32;
   const uint64_t needed = (groups + warps_per_cta - 1) / warps_per_cta;
   const uint64_t grid = shape.grid_ctas < needed ? shape.grid_ctas : (needed ? needed : 1);
-  kern<<<static_cast<unsigned>(grid), shape.cta_threads, smem, stream>>>(
-      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk1, rk2, xp);
-  return cudaGetLastError();
+  return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, static_cast<size_t>(smem), stream,
+                    static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk1, rk2, xp);
 }
 
 }  // namespace

@@ -110,6 +110,17 @@ __device__ __forceinline__ void dec_final(const Tabs& T, State& s, const uint32_
   s = State{f0, f1, f2, f3};
 }
 
+// Programmatic dependent launch (the single-buffer launches set it): a grid
+// lets the next launch in its stream queue its CTAs at once, and each grid
+// fills its tables (from the never-written kDevTables) before waiting for the
+// previous grid's completion and memory, so one call's table fill and launch
+// latency overlap the previous call's last wave.  Both are no-ops for a
+// launch without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_previous() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Fill the replicated tables; warp w writes rows w, w + nwarps, ...
 template <bool kDec>
 __device__ __forceinline__ void fill_tables(uint32_t* sm) {
@@ -157,8 +168,10 @@ __global__ void __launch_bounds__(1024, 1)
                   const __grid_constant__ RoundKeys rk, const __grid_constant__ CtrParams cp) {
   extern __shared__ __align__(16) uint32_t smem[];
   constexpr bool kDec = (OP == Op::kEcbDecrypt);
+  pdl_launch_dependents();
   fill_tables<kDec>(smem);
   __syncthreads();
+  pdl_wait_previous();  // the caller's buffers are touched only after this point
 
   const uint32_t lane = threadIdx.x & 31;
   const char* base = reinterpret_cast<const char*>(smem);
@@ -278,8 +291,10 @@ __global__ void __launch_bounds__(1024, 1)
                              const __grid_constant__ RoundKeys rk,
                              const __grid_constant__ CtrParams cp) {
   extern __shared__ __align__(16) uint32_t smem[];
+  pdl_launch_dependents();
   fill_tables<false>(smem);
   __syncthreads();
+  pdl_wait_previous();  // the caller's buffers are touched only after this point
   const uint32_t lane = threadIdx.x & 31;
   const char* base = reinterpret_cast<const char*>(smem);
   const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};

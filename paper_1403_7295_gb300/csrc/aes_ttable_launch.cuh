@@ -29,9 +29,8 @@ cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint3
   p.whole_runs = runs - runs % warps;
   const uint32_t pieces = ctr_tail_pieces(runs - p.whole_runs, warps);
   p.tail_shift = pieces == 8 ? 3 : pieces == 4 ? 2 : pieces == 2 ? 1 : 0;
-  kern<<<static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream>>>(
-      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, p);
-  return cudaGetLastError();
+  return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream,
+                    static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, p);
 }
 
 template <Op OP, int NR, int BPT>
@@ -42,9 +41,8 @@ cudaError_t launch_one(const void* in, void* out, uint64_t nblocks, uint32_t tai
   const int smem = OP == Op::kEcbDecrypt ? kTtableSmemDec : kTtableSmemEnc;
   cudaError_t e = ensure_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<shape.grid_ctas, shape.cta_threads, smem, stream>>>(
-      static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, cp);
-  return cudaGetLastError();
+  return launch_pdl(kern, shape.grid_ctas, shape.cta_threads, smem, stream, static_cast<const uint4*>(in),
+                    static_cast<uint4*>(out), nblocks, tail, rk, cp);
 }
 
 template <Op OP, int NR>
