@@ -10,6 +10,10 @@ Threads: eight host threads, each on its own stream with its own key, call the
 library at the same time (ctypes releases the GIL around each call); every
 output must equal the oracle's.  This covers the process-wide caches (SM count,
 the shared-memory opt-in per kernel and device) under concurrent first use.
+
+Chain: dependent in-place calls back to back on one stream, with torch
+kernels in between and no synchronisation (the single-buffer launches use
+programmatic dependent launch, so this checks every wait is in place).
 """
 import threading
 
@@ -120,3 +124,33 @@ def test_concurrent_calls_from_host_threads(A, torch, oracle):
         assert np.array_equal(c, want_ctr), t
         assert np.array_equal(e, want_ecb), t
         assert np.array_equal(d, pt[:want_ecb.size]), t
+
+
+def test_dependent_calls_back_to_back_without_sync(A, torch, oracle):
+    """Single-buffer launches may start (and fill their tables) while the
+    previous kernel in the stream finishes; each waits for that grid before
+    it touches memory.  A chain of in-place calls that each read the previous
+    call's output, with torch kernels in between and no synchronisation, must
+    give exactly the oracle's chain."""
+    bits = 128
+    k1, k2 = synth.key_bytes(501, bits), synth.key_bytes(502, bits)
+    ks1, ks2 = A.aes_expand_key(k1), A.aes_expand_key(k2)
+    iv = synth.iv_bytes(503, counter0=0xFFFFFF00)
+    n = (3 << 20) + 4096
+    pt = synth.bytes_np(504, synth.STREAM_DATA, n)
+    x = to_dev(pt)
+    other = torch.empty_like(x)
+    want = pt.copy()
+    for rep in range(6):
+        A.aes_ctr_xcrypt(ks1, iv, x, x)                # in place
+        A.aes_ecb_encrypt(ks2, x, x)                   # reads the CTR output
+        x.add_(rep)                                    # a torch kernel in between (uint8 wraps)
+        A.aes_ecb_decrypt(ks1, x, other)               # another buffer
+        A.aes_xts_encrypt(ks1, ks2, rep, 4096, other, x)
+        want = oracle.ctr_xcrypt(k1, bits, iv, want)
+        want = oracle.ecb_encrypt(k2, bits, want)
+        want = (want.astype(np.uint16) + rep).astype(np.uint8)
+        want = oracle.ecb_decrypt(k1, bits, want)
+        want = oracle.xts(False, k1, k2, bits, 4096, rep, want)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), want)
