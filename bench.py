@@ -493,8 +493,8 @@ def time_graph(torch, b, steps):
 def batched_only(args):
     """Just one batched CTR workload: the varlen one at --batch-msgs messages
     (tile 32768), or with --only small the 1,000,000 packet-sized AES-128
-    messages (tile 8192); --warmup then --steps graph replays (the profiling
-    entries for the batch kernel)."""
+    messages (tile 8192); --cta picks the CTA size (default 1024); --warmup
+    then --steps graph replays (the profiling entries for the batch kernel)."""
     import torch
 
     from paper_1403_7295_gb300 import aes as A
@@ -510,7 +510,7 @@ def batched_only(args):
     in_off, total = B.pack_offsets(lengths)
     data = synth.bytes_torch(3, synth.STREAM_DATA, total, device="cuda")
     b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=wl["key_bits"], ivs=wl["ivs"])
-    b.capture(B.AesBatchConfig(1024, 8192 if small else 32768, 0, 0))
+    b.capture(B.AesBatchConfig(args.cta or 1024, 8192 if small else 32768, 0, 0))
     ms = time_graph(torch, b, args.steps) if args.warmup >= 3 else time_device(torch, b.replay, args.steps, args.warmup)
     gbps = b.total_input_bytes() * args.steps / (ms / 1e3) / 1e9
     name = "1,000,000 packet-sized messages" if small else f"{args.batch_msgs} messages"

@@ -548,13 +548,16 @@ __device__ __forceinline__ void store_partial(uint8_t* p, const uint4& v, uint32
 
 // Input of tile block gr of the current message: a whole block, or the
 // leading `rem` bytes of the last one (zero above).
-// (With AES_BATCH_IN_PADDED the last block is read whole; the bytes past the
-// message are the caller's padding.)
+// (With AES_BATCH_IN_PADDED a ragged last block is read whole: the bytes past
+// the message up to the 16-byte boundary are the caller's padding.  A last
+// block without message bytes, the PKCS#7 block of an aligned length, is
+// never read.)
 template <int OPB>
 __device__ __forceinline__ uint4 load_block(const BatchArgs& a, const Cur& c, uint32_t gr) {
-  if (OPB == kBatchEcbDec || gr < c.f || (a.flags & AES_BATCH_IN_PADDED))
+  const uint32_t rem = (c.nr >> 8) & 0xFFu;
+  if (OPB == kBatchEcbDec || gr < c.f || (rem != 0 && (a.flags & AES_BATCH_IN_PADDED)))
     return __ldcs(reinterpret_cast<const uint4*>(c.src + 16ull * gr));
-  return load_partial(reinterpret_cast<const uint8_t*>(c.src + 16ull * gr), (c.nr >> 8) & 0xFFu);
+  return load_partial(reinterpret_cast<const uint8_t*>(c.src + 16ull * gr), rem);
 }
 
 // Per-thread cache of one CTR counter run (256 aligned counters of one
@@ -865,9 +868,11 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
   const bool full = gr < r.full_end;
   const uint8_t* src = reinterpret_cast<const uint8_t*>(r.src0 + 16ull * gr);
   uint8_t* dst = reinterpret_cast<uint8_t*>(r.dst0 + 16ull * gr);
-  uint4 v;
-  if (OPB == kBatchEcbDec || full || (a.flags & AES_BATCH_IN_PADDED)) v = __ldcs(reinterpret_cast<const uint4*>(src));
-  else v = load_partial(src, rem);
+  uint4 v;  // a ragged last block whole only under AES_BATCH_IN_PADDED; an empty one never
+  if (OPB == kBatchEcbDec || full || (rem != 0 && (a.flags & AES_BATCH_IN_PADDED)))
+    v = __ldcs(reinterpret_cast<const uint4*>(src));
+  else
+    v = load_partial(src, rem);
   if (OPB == kBatchCtr) {
     const uint32_t ctr = r.ctr0 + gr;
     const uint4 q = lds128(rk + kRunWords);  // rk0 word 3, cached run, xr, c10

@@ -272,6 +272,30 @@ def test_batch_modes_in_flight_together(torch, B, oracle):
     oracle_check(B, oracle, ecb, kb, keys, None)
 
 
+@pytest.mark.parametrize("op", [0, 1, 2])
+@pytest.mark.parametrize("cta", [512, 256, 1024])
+def test_batch_all_phases_at_once(torch, B, oracle, op, cta):
+    """Short (1..511 blocks) and long (>= 512) messages in one batch, mixed
+    key sizes and counters, in both builds of the persistent kernel: the
+    tile and per-warp phases run, warps in different phases at the same
+    time; ECB+PKCS#7 lengths of whole blocks exercise the padding block that
+    is never read."""
+    n = 900
+    u = W.uniform_lengths(81 + op, n, 0, 2)
+    lengths = np.where(u == 0, W.uniform_lengths(82, n, 1, 2040),
+                       np.where(u == 1, W.uniform_lengths(83, n, 2100, 8100), W.uniform_lengths(84, n, 8200, 60000)))
+    lengths = lengths.astype(np.uint64)
+    if op == 2:
+        lengths = np.maximum((lengths // np.uint64(16)) * np.uint64(16), np.uint64(16))
+    kb = W.key_sizes(81, n)
+    keys = W.message_keys(81, n)
+    ivs = synth.bytes_np(85, synth.STREAM_NONCE, 16 * n).reshape(n, 16)
+    b = build(B, torch, op, lengths, kb, keys, ivs if op == 0 else None, seed=86)
+    b.submit(config=B.AesBatchConfig(cta, 0, 0, 0))
+    torch.cuda.synchronize()
+    oracle_check(B, oracle, b, kb, keys, ivs)
+
+
 def test_batch_per_message_errors(torch, B, oracle):
     n = 64
     lengths = mixed_lengths(10, n)
