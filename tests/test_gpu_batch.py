@@ -436,3 +436,36 @@ def test_full_size_small_messages_1M(torch, B, oracle):
     assert int((b.status != 0).sum()) == 0
     pick = np.unique((synth.uniform01(21, synth.STREAM_MISC, 2000) * b.n).astype(np.int64))
     oracle_check(B, oracle, b, kb, keys, ivs, idx=list(pick) + [0, b.n - 1])
+
+
+def test_batch_randomized_shapes(torch, B, oracle):
+    """Seeded random trials over everything a caller controls: message count,
+    length mix (empty to 70 KB, so every phase and tile boundary shows up),
+    op, key sizes, counter starts, CTA size (both builds), tile size (kernel-
+    sized or explicit), grid size and the padded flags.  Every message of
+    every trial equals the oracle."""
+    rng = np.random.default_rng(20261204)
+    for trial in range(16):
+        op = int(rng.integers(0, 3))
+        n = int(rng.integers(1, 700))
+        kind = rng.integers(0, 4, n)
+        lengths = np.where(kind == 0, rng.integers(0, 64, n),
+                           np.where(kind == 1, rng.integers(64, 2048, n),
+                                    np.where(kind == 2, rng.integers(2048, 8192, n), rng.integers(8192, 70000, n))))
+        lengths = lengths.astype(np.uint64)
+        if op == 2:
+            lengths = np.maximum((lengths // np.uint64(16)) * np.uint64(16), np.uint64(16))
+        kb = np.array([128, 192, 256], np.uint32)[rng.integers(0, 3, n)]
+        keys = rng.integers(0, 256, (n, 32)).astype(np.uint8)
+        ivs = rng.integers(0, 256, (n, 16)).astype(np.uint8)
+        cta = int(rng.choice([256, 384, 512, 640, 1024]))
+        tile = int(rng.choice([0, cta, 4 * cta, 32 * cta]))
+        grid = int(rng.choice([0, 1, 7, 152, 300]))
+        padded = bool(rng.integers(0, 2))
+        in_off, total = B.pack_offsets(lengths)
+        data = synth.bytes_torch(900 + trial, synth.STREAM_DATA, max(total, 16), device="cuda")
+        b = B.Batch(op, data, in_off, lengths, keys=keys, key_bits=kb, ivs=ivs if op == 0 else None,
+                    padded=None if padded else False)
+        b.submit(config=B.AesBatchConfig(cta, tile, grid, 0))
+        torch.cuda.synchronize()
+        oracle_check(B, oracle, b, kb, keys, ivs)
