@@ -653,11 +653,14 @@ def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
     srv = Server(pool, keys, bits, nonces, budget_bytes=8 << 30, n_streams=2, slots_per_stream=2,
                  max_batch_msgs=8192)
     rep = srv.run(arr, tenants, offs, lengths, time_limit=seconds + 120.0)
+    rep.pop("counters", None)
+    rep["engine"] = "native aes_server_replay (admission, batching, launch and completion in the library)"
     rep.update({"rate_per_s": rate, "seconds": seconds, "key_bits": 256, "tenants": n_t,
                 "budget_bytes": 8 << 30, "offered_gbps": float(lengths.sum()) / seconds / 1e9})
     for k in ("p50_ms", "p99_ms", "max_ms", "gbps", "wall_s", "mean_batch_msgs", "offered_gbps"):
         if rep.get(k) is not None:
             rep[k] = round(rep[k], 3)
+    srv.close()
     del srv, pool
     torch.cuda.empty_cache()
     return rep

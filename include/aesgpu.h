@@ -319,6 +319,98 @@ aes_status aes_file_crypt(const char *src_path, const char *dst_path, aes_file_m
  * pool and stay with that call. */
 void aes_file_trim(void);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching AES-CTR server.  The paper has no counterpart: its
+ * chunks become requests that arrive over time, each run through the batch
+ * kernels with its tenant's resident key schedule.
+ *
+ * aes_server_progress runs one pass of the loop:
+ *  1. frees the output ranges and budget of the completions it handed out in
+ *     the previous call (a completion's output stays readable until then);
+ *  2. admits waiting requests in arrival order while the budget allows: each
+ *     is charged its input and output bytes rounded up to 16, its output range
+ *     comes from a ring arena of the budget's size, and it takes the tenant's
+ *     next counter range (IV = tenant nonce || 32-bit counter, the counter
+ *     advanced by the request's blocks, so no keystream block repeats within
+ *     a tenant until 2^32 blocks);
+ *  3. launches every admitted request into the next batch as soon as one of
+ *     the n_streams x slots_per_stream slots is free (continuous batching);
+ *  4. reports the requests of batches whose event fired.  A batch not
+ *     complete after batch_timeout_s is declared lost: its requests are
+ *     reported with AES_ERR_TIMEOUT, its slot and output ranges are never
+ *     reused, and the server stops admitting (aes_server_healthy returns 0).
+ *
+ * A server is used from one thread at a time.  d_pool (device, 16-byte
+ * aligned, pool_bytes long) holds every request's input at a 16-byte aligned
+ * offset; the caller keeps it alive and unchanged while requests are in
+ * flight.  schedules (host, n_tenants) and nonces (host, 12 bytes per tenant)
+ * are copied at creation.  Device memory held: the output arena
+ * (budget_bytes), the schedule table and per slot max_batch_msgs descriptors
+ * plus a batch workspace; pinned host memory: the descriptor staging of each
+ * slot.  aes_server_destroy waits for the server's streams. */
+typedef struct aes_server aes_server;
+
+typedef struct aes_server_config {
+    uint64_t budget_bytes;      /* bytes admitted at once (input + output per request); 0 = 8 GiB */
+    uint32_t n_streams;         /* 0 = 2 (at most 64) */
+    uint32_t slots_per_stream;  /* batches in flight per stream; 0 = 2 (at most 64) */
+    uint32_t max_batch_msgs;    /* 0 = 8192 */
+    int32_t grid_ctas;          /* persistent-kernel CTAs; 0 = one per SM */
+    double batch_timeout_s;     /* 0 = 10 s */
+    uint64_t inject_lost_batch; /* test hook: the k-th launched batch (1-based) is treated as never
+                                   completing, on the host (its GPU work runs normally); 0 = none */
+} aes_server_config;
+
+typedef struct aes_server_completion {
+    uint64_t id;            /* the caller's request id */
+    int32_t status;         /* AES_OK, or AES_ERR_TIMEOUT (its batch was declared lost) */
+    uint32_t tenant;
+    uint64_t out_off;       /* offset of the output in aes_server_output(), readable until the next progress call */
+    uint64_t length;
+    uint32_t counter;       /* CTR counter of the request's first block */
+    uint32_t reserved;
+    double t_arrival, t_admitted, t_done;  /* seconds on the server's clock (t_done -2 when lost) */
+} aes_server_completion;
+
+typedef struct aes_server_stats {
+    uint64_t submitted, completed, timed_out;
+    uint64_t batches;             /* launched */
+    uint64_t batches_overlapped;  /* launched while earlier batches were still on the GPU */
+    uint64_t bytes;               /* completed request bytes */
+    uint64_t max_charged;         /* peak budget in use */
+    double mean_batch_msgs;
+} aes_server_stats;
+
+aes_status aes_server_create(const aes_server_config *cfg, const void *d_pool, uint64_t pool_bytes,
+                             const aes_key_schedule *schedules, const uint8_t *nonces, uint32_t n_tenants,
+                             aes_server **out);
+void aes_server_destroy(aes_server *s);
+/* Queue one request (arrival = now).  AES_ERR_ARG for a bad tenant, offset or
+ * range; AES_ERR_NOMEM when its input and output bytes exceed the budget. */
+aes_status aes_server_submit(aes_server *s, uint64_t id, uint32_t tenant, uint64_t in_off, uint64_t length);
+/* One pass of the loop; writes up to max_done completions to done and returns
+ * their count (the rest come with later calls).  *status (may be NULL) gets
+ * the pass's status: a failed launch or CUDA error. */
+uint32_t aes_server_progress(aes_server *s, aes_server_completion *done, uint32_t max_done, aes_status *status);
+int aes_server_healthy(const aes_server *s);  /* 0 once a batch was declared lost */
+int aes_server_idle(const aes_server *s);     /* 1: nothing waiting, queued, on the GPU or unreported */
+void *aes_server_output(aes_server *s);       /* device base of the output arena */
+double aes_server_now(const aes_server *s);   /* the server's clock, seconds */
+void aes_server_get_stats(const aes_server *s, aes_server_stats *stats);
+/* Replay an arrival schedule in real time on the calling thread: request i
+ * (id i) arrives arrival_s[i] seconds after the call starts (non-decreasing),
+ * for tenants[i], input at in_offs[i], lengths[i] bytes.  Runs until every
+ * request is reported, a batch is lost and nothing else is in flight, or
+ * time_limit_s passes.  Per request (arrays may be NULL): latency_s (done -
+ * arrival; -1 not completed, -2 lost), wait_s (admission - arrival),
+ * counters (its first CTR counter).  capture (device) with capture_off: the
+ * output of each request whose capture_off is not UINT64_MAX is copied to
+ * capture + capture_off[i] when it completes. */
+aes_status aes_server_replay(aes_server *s, uint64_t n, const double *arrival_s, const uint32_t *tenants,
+                             const uint64_t *in_offs, const uint64_t *lengths, double time_limit_s,
+                             double *latency_s, double *wait_s, uint32_t *counters, void *capture,
+                             const uint64_t *capture_off);
+
 /* The CUDA error code behind the calling thread's last AES_ERR_CUDA (0 if none). */
 int aes_last_cuda_error(void);
 

@@ -1,4 +1,4 @@
-"""GPU tests of the continuous-batching server.
+"""GPU tests of the native continuous-batching server (aes_server_*).
 
 * each request's output, captured when its batch completes, equals the same
   request run alone through the single-buffer CTR call (and, for small ones,
@@ -7,7 +7,10 @@
   before those batches finish (continuous batching, several batches in
   flight);
 * admission never charges more than the device-memory budget, and a budget
-  much smaller than the offered load still completes every request.
+  much smaller than the offered load still completes every request;
+* tenant counters never reuse a keystream block; a lost batch (injected on
+  the host) times out without hanging and stops admission;
+* the online submit / progress API reports every request with its output.
 """
 import numpy as np
 import pytest
@@ -72,19 +75,12 @@ def test_serving_results_equal_alone_and_batches_overlap(torch, oracle):
     n = 3000
     arr, offs, lengths = workload(7, n, pool_bytes, 4 << 20, rate=20000.0)
     tenants = W.tenants(7, arr.size, 64)
-    captured = {}
-
-    def grab(r, view):
-        if r.rid % 25 == 0:
-            captured[r.rid] = (view.clone(), r.iv)
-
-    srv.on_complete = grab
-    rep = srv.run(arr, tenants, offs, lengths, time_limit=60.0)
+    rep = srv.run(arr, tenants, offs, lengths, time_limit=60.0, capture=range(0, arr.size, 25))
     assert rep["completed"] == arr.size
     assert rep["p50_ms"] is not None and rep["p99_ms"] >= rep["p50_ms"]
     assert rep["batches"] > 1
     assert rep["batches_launched_while_previous_in_flight"] > 0
-    check_alone(torch, oracle, srv, pool, keys, bits, captured, tenants, offs, lengths)
+    check_alone(torch, oracle, srv, pool, keys, bits, rep["captured"], tenants, offs, lengths)
 
 
 def test_admission_respects_a_tight_budget(torch, oracle):
@@ -95,17 +91,10 @@ def test_admission_respects_a_tight_budget(torch, oracle):
     n = 400
     arr, offs, lengths = workload(8, n, pool_bytes, 1 << 20, rate=50000.0)
     tenants = W.tenants(8, arr.size, 8)
-    captured = {}
-
-    def grab(r, view):
-        if r.rid % 20 == 0:
-            captured[r.rid] = (view.clone(), r.iv)
-
-    srv.on_complete = grab
-    rep = srv.run(arr, tenants, offs, lengths, time_limit=60.0)
+    rep = srv.run(arr, tenants, offs, lengths, time_limit=60.0, capture=range(0, arr.size, 20))
     assert rep["completed"] == arr.size
     assert rep["max_budget_charged"] <= budget
-    check_alone(torch, oracle, srv, pool, keys, bits, captured, tenants, offs, lengths)
+    check_alone(torch, oracle, srv, pool, keys, bits, rep["captured"], tenants, offs, lengths)
 
 
 def test_tenant_counters_never_reuse_a_keystream_block(torch):
@@ -114,44 +103,55 @@ def test_tenant_counters_never_reuse_a_keystream_block(torch):
     lengths = W.uniform_lengths(9, 200, 1, 5000)
     offs = np.zeros(200, dtype=np.uint64)
     tenants = np.arange(200) % 4
-    ivs = {}
-
-    def grab(r, view):
-        ivs[r.rid] = (r.tenant, int.from_bytes(r.iv[12:], "big"), (r.length + 15) // 16)
-
-    srv.on_complete = grab
-    srv.run(arr, tenants, offs, lengths, time_limit=30.0)
+    rep = srv.run(arr, tenants, offs, lengths, time_limit=30.0)
+    assert rep["completed"] == 200
+    ctr = rep["counters"]
     for t in range(4):
-        ranges = sorted((c, c + nb) for (tt, c, nb) in ivs.values() if tt == t)
+        ranges = sorted((int(ctr[i]), int(ctr[i]) + (int(lengths[i]) + 15) // 16) for i in range(200) if tenants[i] == t)
+        assert ranges[0][0] == 0
         for (a0, a1), (b0, b1) in zip(ranges, ranges[1:]):
-            assert a1 <= b0
-
-
-class _NeverDone:
-    """A completion event that never fires: a lost batch, injected on the host."""
-
-    def query(self):
-        return False
+            assert a1 == b0  # consecutive, never overlapping
 
 
 def test_lost_batch_times_out_without_hanging(torch):
+    """The first batch is declared lost on the host (its GPU work runs; the
+    server is told its completion never comes): after the bounded wait its
+    request fails with a timeout, admission stops, and the replay returns."""
     import time
 
-    from paper_1403_7295_gb300.serve import Request
-
-    srv, pool, keys, bits = setup_server(torch, 4, 16 << 20, 64 << 20, seed=80, batch_timeout_s=0.2)
-    srv.arrive(Request(0, 1, 0, 4096, 0.0))
-    srv.admit(0.0)
-    assert srv.launch(0.0)
-    slot = srv.inflight[0]
-    torch.cuda.synchronize()
-    slot.event = _NeverDone()  # the real work finished; the host never hears of it
+    srv, pool, keys, bits = setup_server(torch, 4, 16 << 20, 64 << 20, seed=80, batch_timeout_s=0.2,
+                                         inject_lost_batch=1)
     t0 = time.perf_counter()
-    while srv.inflight and time.perf_counter() - t0 < 5.0:
-        srv.poll(lambda: time.perf_counter() - t0 + 0.0)
-    assert not srv.inflight and len(srv.timed_out) == 1 and not srv.healthy()
-    assert srv.quarantined and srv.quarantined[0] is slot
-    # the run loop stops admitting and returns instead of waiting forever
-    arr = np.array([0.0, 0.001])
-    rep = srv.run(arr, np.array([0, 1]), np.zeros(2, np.uint64), np.array([32, 32], np.uint64), time_limit=5.0)
+    arr = np.array([0.0, 0.5])  # the second request arrives after the first batch was declared lost
+    rep = srv.run(arr, np.array([0, 1]), np.zeros(2, np.uint64), np.array([4096, 32], np.uint64), time_limit=5.0)
+    assert time.perf_counter() - t0 < 5.0
     assert rep["completed"] == 0 and rep["timed_out"] == 1
+    assert not srv.healthy()
+
+
+def test_online_submit_and_progress(torch, oracle):
+    from paper_1403_7295_gb300 import aes as A
+
+    srv, pool, keys, bits = setup_server(torch, 3, 8 << 20, 32 << 20, seed=90, max_batch_msgs=4)
+    lengths = [1, 15, 16, 17, 4096, 100000, 7, 65536, 3, 12345]
+    offs = [(i * 700000) // 16 * 16 for i in range(len(lengths))]
+    for i, (o, ln) in enumerate(zip(offs, lengths)):
+        srv.submit(1000 + i, i % 3, o, ln)
+    seen = {}
+    for _ in range(100000):
+        for c in srv.progress(max_done=3):
+            assert c.status == 0
+            out = srv.output()[c.out_off: c.out_off + c.length].clone()
+            seen[c.id] = (out, srv.iv(c.tenant, c.counter), c.t_done >= c.t_admitted >= c.t_arrival)
+        if srv.idle():
+            break
+    assert sorted(seen) == [1000 + i for i in range(len(lengths))]
+    torch.cuda.synchronize()
+    for i, (o, ln) in enumerate(zip(offs, lengths)):
+        out, iv, ordered = seen[1000 + i]
+        t = i % 3
+        assert ordered
+        ks = A.aes_expand_key(keys[t][: bits[t] // 8], int(bits[t]))
+        assert torch.equal(out, A.aes_ctr_xcrypt(ks, iv, pool[o: o + ln])), i
+    st = srv.stats()
+    assert st["completed"] == len(lengths) and st["batches"] >= 3
