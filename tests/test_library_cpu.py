@@ -171,3 +171,26 @@ def test_file_crypt_validation_and_empty_file(lib, tmp_path):
     assert L.aes_file_crypt(s, d, 0, kr, ivb, None, ctypes.byref(st)) == 0
     assert dst.exists() and dst.stat().st_size == 0 and st.bytes == 0 and st.chunks == 0
     L.aes_file_trim()  # nothing pinned yet: a no-op without a GPU
+
+
+def test_server_validation_without_a_gpu(lib):
+    """aes_server_*: argument checks that fail before any CUDA call, and the
+    null-handle behaviour of the query calls."""
+    from paper_1403_7295_gb300 import serve as S
+
+    L = S._declare()
+    ks = A.aes_expand_key(synth.key_bytes(0, 128))
+    nonces = (ctypes.c_uint8 * 12)()
+    h = ctypes.c_void_p()
+    base = 1 << 20  # never dereferenced
+    assert L.aes_server_create(None, base, 4096, ctypes.byref(ks), nonces, 0, ctypes.byref(h)) == 1  # no tenants
+    assert L.aes_server_create(None, None, 4096, ctypes.byref(ks), nonces, 1, ctypes.byref(h)) == 1  # no pool
+    assert L.aes_server_create(None, base, 4096, None, nonces, 1, ctypes.byref(h)) == 1             # no schedules
+    cfg = S.ServerConfig(1 << 20, 65, 2, 16, 0, 1.0, 0)                                          # too many streams
+    assert L.aes_server_create(ctypes.byref(cfg), base, 4096, ctypes.byref(ks), nonces, 1, ctypes.byref(h)) == 1
+    assert L.aes_server_submit(None, 0, 0, 0, 16) == 1
+    st = ctypes.c_int(0)
+    assert L.aes_server_progress(None, None, 0, ctypes.byref(st)) == 0 and st.value == 1
+    assert L.aes_server_healthy(None) == 0 and L.aes_server_idle(None) == 0
+    assert L.aes_server_output(None) is None
+    L.aes_server_destroy(None)
