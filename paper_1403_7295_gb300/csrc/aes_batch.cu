@@ -504,9 +504,7 @@ __device__ __forceinline__ void select_message(const Slot* slots, uint32_t wn, u
   c.s = static_cast<uint32_t>(bs - t0);
   c.e = static_cast<uint32_t>(be - t0);
   c.f = static_cast<uint32_t>(bf - t0);
-  // bit 17: long message (>= 512 blocks): CTR caches counter runs for it
-  c.nr = sl.nr | (sl.rem << 8) | ((sl.blk_end <= t1 ? 1u : 0u) << 16) |
-         ((sl.blk_end - sl.blk_start >= 512 ? 1u : 0u) << 17);
+  c.nr = sl.nr | (sl.rem << 8) | ((sl.blk_end <= t1 ? 1u : 0u) << 16);
   c.ctr = sl.ctr_base + static_cast<uint32_t>(t0);
   c.slot = lo;
   c.src = sl.src0 + 16 * t0;
@@ -578,13 +576,7 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
   uint8_t* dst = reinterpret_cast<uint8_t*>(c.dst + 16ull * gr);
   if (OPB == kBatchCtr) {
     const uint32_t ctr = c.ctr + gr;
-    State s;
-    if (!((c.nr >> 17) & 1u)) {  // short message: round 1 folded per message, rounds 2.. in full
-      const uint32_t x = __byte_perm(ctr, 0, 0x0123) ^ rk[kCtrRk0w3];
-      const uint4 c1 = lds128(rk + kCtrC1);
-      s = State{c1.x ^ T.t3(x), c1.y ^ T.t2(x), c1.z ^ T.t1(x), c1.w ^ T.t0(x)};
-      s = enc_any(T, s, rk, nr, 2);
-    } else {
+    // tile-phase messages are long (>= kShortMax blocks): counter runs are cached per lane
     if ((ctr >> 8) != rc.run || c.slot + 1 != rc.slot) {  // a new run: its round-1/2 constants
       rc.run = ctr >> 8;
       rc.slot = c.slot + 1;
@@ -599,9 +591,8 @@ __device__ __forceinline__ void process_block(const BatchArgs& a, const Tabs& T,
       rc.d3 = k2.w ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
     }
     const uint32_t s0 = rc.c10 ^ T.t3(rc.xr ^ ((ctr & 255u) << 24));
-    s = State{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
+    State s{rc.d0 ^ T.t0(s0), rc.d1 ^ T.t3(s0), rc.d2 ^ T.t2(s0), rc.d3 ^ T.t1(s0)};
     s = enc_any(T, s, rk, nr, 3);
-    }
     if (full || (a.flags & AES_BATCH_OUT_PADDED)) {
       __stcs(reinterpret_cast<uint4*>(dst),
              make_uint4(v_in.x ^ s.s0, v_in.y ^ s.s1, v_in.z ^ s.s2, v_in.w ^ s.s3));
@@ -1110,8 +1101,7 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
           // every lane takes the message of the span's first block; if that
           // message holds the whole span in whole blocks, run the fast loop
           if (span < c.s || span >= c.e) select_message(slots, wn, t0, t1, span, c);
-          const bool whole = span >= c.s && span + 256 <= c.f &&
-                             (OPB != kBatchCtr || ((c.nr >> 17) & 1u));
+          const bool whole = span >= c.s && span + 256 <= c.f;
           if (whole) {
             const uint32_t* rk = rk_all + c.slot * kRkStride;
             switch (c.nr & 0xFFu) {
