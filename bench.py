@@ -320,28 +320,42 @@ def gpu_arm(args):
     }
     if rank == 0:
         blocks = nbytes / 16
-        lk = lookups_per_block(bits) * blocks
-        g_lookups = lk / per_launch_s / 1e9
         clock_mhz = sm_max_mhz
-        rl = {"bound": "alu", "unit": "Glookup/s", "achieved": round(g_lookups, 1),
-              "peak": None, "frac": None, "traffic": read_traffic(args),
-              "ops_per_block": lookups_per_block(bits),
-              "pipe": "32-bit shared-memory loads (replicated T-table lookups)",
-              "hbm_gbps_moved": round(2 * nbytes / per_launch_s / 1e9, 1),
-              "hbm_peak_gbps": hbm_peak, "hbm_frac": round(2 * nbytes / per_launch_s / 1e9 / hbm_peak, 4),
-              "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json copy bandwidth)" if peak_src == "measured"
-              else "fallback 6.8 TB/s"}
-        if probes and probes.get("lds32"):
-            peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
-            rl["peak"] = round(peak, 1)
-            rl["frac"] = round(g_lookups / peak, 4)
-            measured = read_profile_field(args, "lookups_per_block_measured:")
-            if measured:
-                # the kernel's own lookups (CTR caching does fewer than 16*Nr): how busy the pipe is
-                rl["lookups_per_block_measured"] = measured
-                rl["pipe_frac"] = round(measured * blocks / per_launch_s / 1e9 / peak, 4)
-            rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
-                                 f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
+        hbm = {"hbm_gbps_moved": round(2 * nbytes / per_launch_s / 1e9, 1),
+               "hbm_peak_gbps": hbm_peak, "hbm_frac": round(2 * nbytes / per_launch_s / 1e9 / hbm_peak, 4),
+               "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json copy bandwidth)" if peak_src == "measured"
+               else "fallback 6.8 TB/s"}
+        if args.variant == 2:
+            # bitsliced rounds: no lookups; bound by the ALU pipe (LOP3 / PRMT / SHF)
+            ops = read_profile_field(args, "thread_instructions_per_block_measured:")
+            rl = {"bound": "alu", "unit": "Gop/s", "achieved": None, "peak": None, "frac": None,
+                  "traffic": read_traffic(args), "ops_per_block": ops,
+                  "pipe": "64-lane ALU pipe (LOP3, PRMT, SHF of the bitsliced circuit)", **hbm}
+            if ops and probes and probes.get("lop3"):
+                peak = probes["lop3"] * sms * clock_mhz * 1e6 / 1e9
+                rl["achieved"] = round(ops * blocks / per_launch_s / 1e9, 1)
+                rl["peak"] = round(peak, 1)
+                rl["frac"] = round(rl["achieved"] / peak, 4)
+                rl["peak_source"] = (f"measured probe: {probes['lop3']} LOP3 per clock per SM x {sms} SMs "
+                                     f"x {clock_mhz:.0f} MHz (max SM clock)")
+        else:
+            lk = lookups_per_block(bits) * blocks
+            g_lookups = lk / per_launch_s / 1e9
+            rl = {"bound": "alu", "unit": "Glookup/s", "achieved": round(g_lookups, 1),
+                  "peak": None, "frac": None, "traffic": read_traffic(args),
+                  "ops_per_block": lookups_per_block(bits),
+                  "pipe": "32-bit shared-memory loads (replicated T-table lookups)", **hbm}
+            if probes and probes.get("lds32"):
+                peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
+                rl["peak"] = round(peak, 1)
+                rl["frac"] = round(g_lookups / peak, 4)
+                measured = read_profile_field(args, "lookups_per_block_measured:")
+                if measured:
+                    # the kernel's own lookups (CTR caching does fewer than 16*Nr): how busy the pipe is
+                    rl["lookups_per_block_measured"] = measured
+                    rl["pipe_frac"] = round(measured * blocks / per_launch_s / 1e9 / peak, 4)
+                rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
+                                     f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
         result["roofline"] = rl
         dist_steps["gbps_at_median"] = round(nbytes / (dist_steps["median_ms"] / 1e3) / 1e9, 2)
         dist_steps["how"] = ("one event pair per launch, after the timed region (rank 0); the timed "
@@ -381,18 +395,32 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# The committed ncu summary of each round implementation's AES-128 CTR kernel,
+# with the sources whose hash it records (numbers from a stale summary are
+# not used).
+PROFILE_OF_VARIANT = {
+    0: ("ttable_ctr_aes128_1GiB.md", ["aes_ttable.cuh"]),
+    1: ("ttable_ctr_aes128_1GiB.md", ["aes_ttable.cuh"]),
+    2: ("bitslice_ctr_aes128_256MiB.md", ["aes_bitslice.cu", "aes_bitslice_circuit.cuh"]),
+}
+
+
 def read_profile_field(args, key):
-    """A number from the committed ncu summary of the default kernel, if the
-    summary still matches the kernel source and this run uses that kernel."""
+    """A number from the committed ncu summary of the kernel this run uses
+    (AES-128 CTR only), if the summary still matches the kernel's source."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "ttable_ctr_aes128_1GiB.md")
-    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128 or args.bpt or args.variant:
+    if args.mode != "ctr" or args.bits != 128 or args.bpt or args.variant not in PROFILE_OF_VARIANT:
         return None
-    src = os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", "aes_ttable.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    name, sources = PROFILE_OF_VARIANT[args.variant]
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", src), "rb").read())
     text = open(path).read()
-    if f"source_sha256_16: {sha}" not in text:
+    if f"source_sha256_16: {h.hexdigest()[:16]}" not in text:
         return None
     for ln in text.splitlines():
         if ln.startswith(key):
@@ -401,25 +429,11 @@ def read_profile_field(args, key):
 
 
 def read_traffic(args):
-    """dram bytes per launch from the committed ncu summary, if it still
-    matches the kernel source; else null."""
-    import hashlib
-
-    path = os.path.join(ROOT, "profiles", "ttable_ctr_aes128_1GiB.md")
-    if not os.path.exists(path) or args.mode != "ctr" or args.bits != 128 or args.bpt or args.variant:
-        return None
-    src = os.path.join(ROOT, "paper_1403_7295_gb300", "csrc", "aes_ttable.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    per_gib = None
-    for ln in open(path):
-        if ln.startswith("traffic_bytes_per_GiB_launch:"):
-            parts = ln.split()
-            per_gib = float(parts[1])
-            if "source_sha256_16:" in parts and parts[parts.index("source_sha256_16:") + 1] != sha:
-                return None
-    if per_gib is None:
-        return None
-    return per_gib * (args.size_mib / 1024)
+    """dram bytes per launch from the committed ncu summary (scaled from its
+    per-GiB figure to this buffer), if it still matches the kernel source;
+    else null."""
+    per_gib = read_profile_field(args, "traffic_bytes_per_GiB_launch:")
+    return None if per_gib is None else per_gib * (args.size_mib / 1024)
 
 
 def modes_arm(torch, A, x, y):

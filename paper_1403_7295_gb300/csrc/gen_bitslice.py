@@ -6,26 +6,37 @@ Route (FIPS-197 §5.1.1 defines SubBytes as inversion in GF(2^8) followed by
 an affine map; the inversion is computed here in a tower of fields):
 
   GF(4)   = GF(2)[W] / (W^2 + W + 1)
-  GF(16)  = GF(4)[Z] / (Z^2 + Z + mu),      mu = W
-  GF(256) = GF(16)[Y] / (Y^2 + Y + lam),    lam: the first GF(16) constant
-                                            making the polynomial irreducible
+  GF(16)  = GF(4)[Z] / (Z^2 + Z + mu),      mu = W or W^2
+  GF(256) = GF(16)[Y] / (Y^2 + Y + lam),    lam: a GF(16) constant making
+                                            the polynomial irreducible
   inverse of h*Y + l:  d = (h^2*lam + h*l + l^2)^-1,  result (h*d)*Y + (h+l)*d
   inverse in GF(16) the same way over GF(4); inverse in GF(4) = squaring.
 
-An isomorphism T from the AES polynomial basis to the tower basis is found
-by searching the tower field for a root of x^8 + x^4 + x^3 + x + 1.  Then
+An isomorphism T from the AES polynomial basis to the tower basis maps x to
+a root beta of x^8 + x^4 + x^3 + x + 1 in the tower field.  Then
   S(x)    = A . T^-1 . inv(T . x) + 0x63
   S^-1(y) = T^-1 . inv(T . A^-1 . (y + 0x63))
 with A the affine matrix.  Every signal is tracked as a set of "atoms"
-(input bits and AND outputs) combined by XOR; XOR networks are emitted on
-demand with reuse of already-built combinations, and the whole circuit is
-evaluated on all 256 inputs before anything is written.
+(input bits and AND outputs) combined by XOR.  The XOR networks between AND
+layers are built as short linear programs with the distance-based greedy
+heuristic of Boyar and Peralta: each new XOR is the sum of two signals
+already built that most reduces the total distance of the layer's targets
+(the distance of a target being how many built signals must still be added
+to reach it; exact, from a table over the layer's span).  The whole circuit
+is evaluated on all 256 inputs before anything is written.
+
+The choice of mu, lam and beta changes the gate count; PARAMS holds, for each
+direction, the choice with the fewest gates over all of them (found by
+`python gen_bitslice.py --search`, about two minutes).
 
 Usage: python gen_bitslice.py   (writes aes_bitslice_circuit.cuh beside itself)
 """
 from __future__ import annotations
 
 import os
+import sys
+
+import numpy as np
 
 AES_POLY = 0x11B
 
@@ -78,7 +89,8 @@ def g4_mul(a, b):
     return (hi << 1) | lo
 
 
-MU = 2  # W
+MU = 2  # W; set by configure()
+LAM = 0  # set by configure()
 
 
 def g16_mul(a, b):
@@ -88,15 +100,20 @@ def g16_mul(a, b):
     return (hi << 2) | lo
 
 
-def _pick_lambda():
+def lambdas():
+    """The lam making Y^2 + Y + lam irreducible over the current GF(16)."""
     squares_plus = {g16_mul(y, y) ^ y for y in range(16)}
-    for lam in range(1, 16):
-        if lam not in squares_plus:
-            return lam
-    raise RuntimeError("no irreducible Y^2 + Y + lam")
+    return [lam for lam in range(1, 16) if lam not in squares_plus]
 
 
-LAM = _pick_lambda()
+def configure(mu: int, lam: int) -> None:
+    global MU, LAM
+    if mu not in (2, 3):
+        raise ValueError("mu must be W (2) or W^2 (3)")
+    MU = mu
+    if lam not in lambdas():
+        raise ValueError(f"Y^2 + Y + {lam:#x} is reducible")
+    LAM = lam
 
 
 def g256_mul(a, b):
@@ -113,29 +130,27 @@ def g256_pow(a, e):
     return r
 
 
-def find_isomorphism():
-    """8x8 matrix T (list of 8 column ints) with T(x^i) = beta^i, beta a root
-    of the AES polynomial in the tower field, checked to be multiplicative."""
-    for beta in range(2, 256):
-        # beta^8 + beta^4 + beta^3 + beta + 1 == 0
-        v = g256_pow(beta, 8) ^ g256_pow(beta, 4) ^ g256_pow(beta, 3) ^ beta ^ 1
-        if v != 0:
-            continue
-        cols = [g256_pow(beta, i) for i in range(8)]
+def roots():
+    """Roots of the AES polynomial in the current tower field."""
+    return [b for b in range(2, 256)
+            if g256_pow(b, 8) ^ g256_pow(b, 4) ^ g256_pow(b, 3) ^ b ^ 1 == 0]
 
-        def T(x, cols=cols):
-            r = 0
-            for i in range(8):
-                if (x >> i) & 1:
-                    r ^= cols[i]
-            return r
 
-        if len({T(x) for x in range(256)}) != 256:
-            continue
-        ok = all(T(aes_mul(a, b)) == g256_mul(T(a), T(b)) for a in range(0, 256, 3) for b in range(0, 256, 7))
-        if ok:
-            return cols, T
-    raise RuntimeError("no isomorphism found")
+def isomorphism(beta: int):
+    """8x8 matrix T (list of 8 column ints) with T(x^i) = beta^i, checked to
+    be a bijection and multiplicative."""
+    if beta not in roots():
+        raise ValueError(f"{beta:#x} is not a root of the AES polynomial")
+    cols = [g256_pow(beta, i) for i in range(8)]
+
+    def T(x):
+        return mat_apply(cols, x)
+
+    if len({T(x) for x in range(256)}) != 256:
+        raise ValueError("not a bijection")
+    if not all(T(aes_mul(a, b)) == g256_mul(T(a), T(b)) for a in range(0, 256, 3) for b in range(0, 256, 7)):
+        raise ValueError("not multiplicative")
+    return cols, T
 
 
 def mat_apply(cols, x):
@@ -162,8 +177,8 @@ class Circuit:
     input slices (99 = all-ones when a constant is needed); AND gates create
     new atoms.  Building only records the AND gates and outputs; `finish`
     then emits the XOR networks layer by layer (AND depth), each layer's
-    operand combinations reduced with Paar's greedy common-pair elimination
-    and earlier XOR nodes reused where one is contained in a target."""
+    operand combinations built as one short linear program (see _reduce),
+    starting from the atoms and every earlier XOR node in their span."""
 
     def __init__(self, prefix="t"):
         self.prefix = prefix
@@ -198,48 +213,50 @@ class Circuit:
         return name
 
     def _reduce(self, targets):
-        """Build every target (set of atoms) with few XORs; returns {target: name}."""
-        # each working target: set of variable names still to combine
-        work = {}
-        for t in targets:
-            if t in self.built:
-                continue
-            rem = set(t)
-            vars_ = set()
-            # reuse the largest earlier XOR nodes contained in the target
-            while True:
-                best = None
-                for k, name in self.built.items():
-                    if len(k) > 1 and k <= rem and (best is None or len(k) > len(best[0])):
-                        best = (k, name)
-                if best is None:
-                    break
-                rem -= best[0]
-                vars_.add(best[1])
-            vars_ |= {self.atoms[a] for a in rem}
-            work[t] = vars_
-        # Paar: repeatedly combine the most frequent pair
-        while True:
-            counts = {}
-            for vs in work.values():
-                if len(vs) < 2:
-                    continue
-                lst = sorted(vs)
-                for i in range(len(lst)):
-                    for j in range(i + 1, len(lst)):
-                        counts[(lst[i], lst[j])] = counts.get((lst[i], lst[j]), 0) + 1
-            if not counts:
-                break
-            pair = max(sorted(counts), key=lambda k: counts[k])
-            w = self._xor(*pair)
-            for vs in work.values():
-                if pair[0] in vs and pair[1] in vs:
-                    vs.discard(pair[0])
-                    vs.discard(pair[1])
-                    vs.add(w)
-        for t, vs in work.items():
-            (name,) = vs
-            self.built[t] = name
+        """Build every target (set of atoms) with few XORs; returns {target: name}.
+
+        Signals are vectors over the targets' atoms (bit i = atom i of the
+        sorted support).  The base starts as those atoms plus every signal
+        already built inside their span.  ell[v] is the least number of base
+        signals summing to v, for every v of the span; adding s to the base
+        gives ell'[v] = min(ell[v], 1 + ell[v ^ s]) exactly (s is used at
+        most once).  Each step adds the pair sum that is itself a target, or
+        else the one giving the smallest total of ell over the targets (ties:
+        the largest sum of squares, so that near targets finish first)."""
+        todo = [t for t in targets if t not in self.built]
+        if todo:
+            support = sorted(set().union(*todo))
+            idx = {a: i for i, a in enumerate(support)}
+            span = set(support)
+
+            def vec(sig):
+                return sum(1 << idx[a] for a in sig)
+
+            base = {1 << idx[a]: self.atoms[a] for a in support}
+            for sig, name in self.built.items():
+                if len(sig) > 1 and sig <= span:
+                    base.setdefault(vec(sig), name)
+            every = np.arange(1 << len(support), dtype=np.int64)
+            ell = np.full(every.size, 1 << 14, dtype=np.int32)
+            ell[0] = 0
+            for b in base:
+                ell = np.minimum(ell, ell[every ^ b] + 1)
+            F = np.array(sorted({vec(t) for t in todo}), dtype=np.int64)
+            while (ell[F] > 1).any():
+                B = np.array(list(base), dtype=np.int64)
+                ii, jj = np.triu_indices(B.size, 1)
+                S = B[ii] ^ B[jj]
+                fresh = np.array([v not in base for v in S.tolist()])
+                S, ii, jj = S[fresh], ii[fresh], jj[fresh]
+                new = np.minimum(ell[F][:, None], 1 + ell[F[:, None] ^ S[None, :]])
+                is_target = (S[None, :] == F[:, None]).any(axis=0)
+                total = new.sum(axis=0) - (1 << 20) * is_target
+                c = np.lexsort((-(new.astype(np.int64) ** 2).sum(axis=0), total))[0]
+                s = int(S[c])
+                base[s] = self._xor(base[int(B[ii[c]])], base[int(B[jj[c]])])
+                ell = np.minimum(ell, ell[every ^ s] + 1)
+            for t in todo:
+                self.built[t] = base[vec(t)]
         return {t: self.built[t] for t in targets}
 
     def finish(self, outputs):
@@ -278,9 +295,9 @@ def s4_mul(c, a, b):
     return (X(r, q), X(p, q))
 
 
-def s4_scale_mu(a):  # times W
+def s4_scale_mu(a):  # times mu: W (a1 W + a0) = (a1 + a0) W + a1;  W^2 (a1 W + a0) = a0 W + (a1 + a0)
     a1, a0 = a
-    return (X(a1, a0), a1)
+    return (X(a1, a0), a1) if MU == 2 else (a0, X(a1, a0))
 
 
 def s4_sq(a):  # squaring (= inversion in GF(4))
@@ -355,8 +372,14 @@ def linear_on_sigs(sigs, cols):
     return out
 
 
-def build(inverse: bool):
-    cols, T = find_isomorphism()
+# (mu, lam, beta) per direction: the fewest gates found by search()
+PARAMS = {False: (2, 0xA, 0x68), True: (2, 0xC, 0x42)}
+
+
+def build(inverse: bool, params=None):
+    mu, lam, beta = params if params is not None else PARAMS[inverse]
+    configure(mu, lam)
+    cols, T = isomorphism(beta)
     Tinv = mat_inverse(cols)
     A = mat_from_fn(lambda v: affine(v) ^ 0x63)  # linear part of the affine map
     Ainv = mat_inverse(A)
@@ -420,15 +443,43 @@ def emit(c: Circuit, names, const, fname: str) -> str:
             + "\n".join(pre + body) + "\n}\n")
 
 
+def check(c: Circuit, names, const, table, what: str) -> None:
+    for x in range(256):
+        got = evaluate(c, names, const, x)
+        if got != table[x]:
+            raise SystemExit(f"{what}: circuit wrong at {x}: {got} != {table[x]}")
+
+
+def search() -> None:
+    """Gate counts for every (mu, lam, beta); prints the best per direction."""
+    best = {}
+    for mu in (2, 3):
+        configure(mu, lambdas()[0])
+        for lam in lambdas():
+            configure(mu, lam)
+            for beta in roots():
+                for inverse, table in ((False, SBOX), (True, INV_SBOX)):
+                    c, names, const = build(inverse, (mu, lam, beta))
+                    check(c, names, const, table, f"{(mu, lam, beta)}")
+                    gates = c.n_and + c.n_xor
+                    print(f"inverse={inverse} mu={mu} lam={lam:#x} beta={beta:#x}: "
+                          f"{c.n_and} AND + {c.n_xor} XOR", flush=True)
+                    if inverse not in best or gates < best[inverse][0]:
+                        best[inverse] = (gates, (mu, lam, beta))
+    for inverse in (False, True):
+        gates, (mu, lam, beta) = best[inverse]
+        print(f"best {'inverse' if inverse else 'forward'}: ({mu}, {lam:#x}, {beta:#x}), {gates} gates")
+
+
 def main():
     out = []
+    params = []
     for inverse, fname, table in ((False, "bs_sbox", SBOX), (True, "bs_inv_sbox", INV_SBOX)):
         c, names, const = build(inverse)
-        for x in range(256):
-            got = evaluate(c, names, const, x)
-            if got != table[x]:
-                raise SystemExit(f"{fname}: circuit wrong at {x}: {got} != {table[x]}")
+        check(c, names, const, table, fname)
         out.append(emit(c, names, const, fname))
+        mu, lam, beta = PARAMS[inverse]
+        params.append(f"// {fname}: mu = {'W' if mu == 2 else 'W^2'}, lambda = {lam:#x}, beta = {beta:#x}\n")
         print(f"{fname}: {c.n_and} AND, {c.n_xor} XOR, verified on all 256 inputs")
     header = (
         "// aes_bitslice_circuit.cuh — GENERATED by gen_bitslice.py; do not edit.\n"
@@ -436,8 +487,11 @@ def main():
         "// SubBytes and InvSubBytes (FIPS-197 §5.1.1, §5.3.2) as Boolean circuits on\n"
         "// bit-slice words: x{j} holds bit j (bit 0 = least significant) of the byte\n"
         "// being substituted, one independent byte per bit position of W.  Built\n"
-        f"// from inversion in the tower field GF(((2^2)^2)^2) with mu = W, lambda = {LAM:#x}\n"
-        "// (see the generator), checked on all 256 inputs before emission.\n"
+        "// from inversion in the tower field GF(((2^2)^2)^2), with XOR layers as\n"
+        "// short linear programs (see the generator), checked on all 256 inputs\n"
+        "// before emission.  Tower parameters and the root beta that fixes the\n"
+        "// isomorphism from the AES basis:\n"
+        + "".join(params) +
         "#pragma once\n\n"
         "#if defined(__CUDACC__)\n#define AESGPU_BS_HD __host__ __device__ __forceinline__\n"
         "#else\n#define AESGPU_BS_HD inline\n#endif\n\n"
@@ -449,4 +503,7 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if "--search" in sys.argv[1:]:
+        search()
+    else:
+        main()
