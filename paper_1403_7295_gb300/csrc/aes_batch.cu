@@ -280,23 +280,28 @@ __device__ void expand_key(const Tabs& T, const char* sb, uint32_t sb_off, const
 
 // Turn an encryption schedule into the equivalent inverse cipher's (FIPS-197
 // §5.3.5), in place.  InvMixColumns(w) = sum_i TDi[S(byte i of w)], since each
-// td word applies the inverse S-box first.
-__device__ void to_decrypt_schedule(const Tabs& T, const char* sb, uint32_t sb_off, uint32_t nr,
-                                    uint32_t* rk) {
+// td word applies the inverse S-box first.  One unit (r <= nr / 2, column c)
+// swaps word c of rounds r and nr - r, applying InvMixColumns to each unless
+// it lands in round 0 or nr; units touch disjoint words, so they may run on
+// different threads at once.
+__device__ __forceinline__ void decrypt_schedule_unit(const Tabs& T, const char* sb, uint32_t sb_off,
+                                                      uint32_t nr, uint32_t* rk, uint32_t r, uint32_t c) {
   auto inv_mix = [&](uint32_t w) {
     const uint32_t s = sub_word(T, sb, sb_off, w);
     return T.t0(s) ^ T.t1(s) ^ T.t2(s) ^ T.t3(s);
   };
-  for (uint32_t r = 0; r <= nr / 2; ++r) {
-    const uint32_t q = nr - r;
-    for (uint32_t c = 0; c < 4; ++c) {
-      const uint32_t a = rk[4 * r + c], b = rk[4 * q + c];
-      const uint32_t na = (q == 0 || q == nr) ? b : inv_mix(b);  // new round r from old round q
-      const uint32_t nb = (r == 0 || r == nr) ? a : inv_mix(a);  // new round q from old round r
-      rk[4 * r + c] = na;
-      if (q != r) rk[4 * q + c] = nb;
-    }
-  }
+  const uint32_t q = nr - r;
+  const uint32_t a = rk[4 * r + c], b = rk[4 * q + c];
+  const uint32_t na = (q == 0 || q == nr) ? b : inv_mix(b);  // new round r from old round q
+  const uint32_t nb = (r == 0 || r == nr) ? a : inv_mix(a);  // new round q from old round r
+  rk[4 * r + c] = na;
+  if (q != r) rk[4 * q + c] = nb;
+}
+
+__device__ void to_decrypt_schedule(const Tabs& T, const char* sb, uint32_t sb_off, uint32_t nr,
+                                    uint32_t* rk) {
+  for (uint32_t r = 0; r <= nr / 2; ++r)
+    for (uint32_t c = 0; c < 4; ++c) decrypt_schedule_unit(T, sb, sb_off, nr, rk, r, c);
 }
 
 __device__ __forceinline__ uint4 lds128(const uint32_t* p) {
@@ -948,6 +953,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       if (lane >= static_cast<uint32_t>(o)) incl += y;
     }
     const uint32_t nblk = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t dec_nr = 0;  // rounds of this lane's message when its schedule still needs inverting
     if (nb > 0) {
       const uint32_t m = static_cast<uint32_t>(m0 + lane);
       const uint32_t b0 = incl - nb;
@@ -958,7 +964,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
         const uint32_t nk = a.key_bits[m] / 32;
         nr = nk + 6;
         expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, rk);
-        if (OPB == kBatchEcbDec) to_decrypt_schedule(T, sb, sb_off, nr, rk);
+        dec_nr = nr;  // decryption: the whole warp inverts the schedules below
       } else {
         const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
         nr = ks.nr;
@@ -1005,6 +1011,18 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       first[ci] = b0;
     }
     __syncwarp();
+    if (OPB == kBatchEcbDec && a.keys != nullptr) {
+      // Equivalent-inverse-cipher schedules: slot j's units (round r = lane / 4
+      // <= nr / 2, column lane % 4) on the warp's lanes, one slot at a time,
+      // instead of one lane working through a whole schedule alone.
+#pragma unroll 1
+      for (uint32_t j = 0; j < G; ++j) {
+        const uint32_t nr_j = __shfl_sync(0xffffffffu, dec_nr, j);
+        if (nr_j != 0 && lane / 4 <= nr_j / 2)
+          decrypt_schedule_unit(T, sb, sb_off, nr_j, wrk + j * kShortStride<OPB>, lane / 4, lane % 4);
+      }
+      __syncwarp();
+    }
     const uint32_t ng = __popc(valid);
     const uint32_t my_first = lane < ng ? first[lane] : 0xFFFFFFFFu;
     uint32_t cur = 0xFFFFFFFFu;
