@@ -953,27 +953,40 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       if (lane >= static_cast<uint32_t>(o)) incl += y;
     }
     const uint32_t nblk = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t dec_nr = 0;  // rounds of this lane's message when its schedule still needs inverting
+    uint32_t nr = 0;  // the lane's message's rounds (0: no message)
+    const uint32_t* sched = nullptr;  // its resident schedule, copied below by the whole warp
+    if (nb > 0) {
+      const uint32_t m = static_cast<uint32_t>(m0 + lane);
+      if (a.keys != nullptr) {
+        const uint32_t nk = a.key_bits[m] / 32;
+        nr = nk + 6;
+        expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, wrk + lane * kShortStride<OPB>);
+      } else {
+        const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
+        nr = ks.nr;
+        sched = OPB == kBatchEcbDec ? ks.rk_dec : ks.rk_enc;
+      }
+    }
+    if (a.keys == nullptr) {
+      // Resident schedules: slot j's 4(nr + 1) words as coalesced loads by the
+      // warp's lanes (a lane copying its own would issue 60 scattered loads).
+#pragma unroll 1
+      for (uint32_t j = 0; j < G; ++j) {
+        const uint32_t nw = min(4 * (__shfl_sync(0xffffffffu, nr, j) + 1), 60u);  // nr was validated: 10, 12, 14
+        const uint64_t p = __shfl_sync(0xffffffffu, reinterpret_cast<uint64_t>(sched), j);
+        if (nw > 4) {
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(p);
+          uint32_t* dst = wrk + j * kShortStride<OPB>;
+          for (uint32_t w = lane; w < nw; w += 32) dst[w] = __ldg(src + w);
+        }
+      }
+    }
+    __syncwarp();
     if (nb > 0) {
       const uint32_t m = static_cast<uint32_t>(m0 + lane);
       const uint32_t b0 = incl - nb;
       const uint32_t ci = __popc(valid & ((1u << lane) - 1));
       uint32_t* rk = wrk + lane * kShortStride<OPB>;
-      uint32_t nr;
-      if (a.keys != nullptr) {
-        const uint32_t nk = a.key_bits[m] / 32;
-        nr = nk + 6;
-        expand_key(T, sb, sb_off, a.keys + 32ull * m, nk, rk);
-        dec_nr = nr;  // decryption: the whole warp inverts the schedules below
-      } else {
-        const aes_key_schedule& ks = a.schedules[a.sched_idx[m]];
-        nr = ks.nr;
-        const uint32_t* src = OPB == kBatchEcbDec ? ks.rk_dec : ks.rk_enc;
-        const uint32_t nw = 4 * (nr + 1);
-#pragma unroll
-        for (uint32_t i = 0; i < 60; ++i)
-          if (i < nw) rk[i] = __ldg(src + i);
-      }
       GroupMsg r;
       r.src0 = reinterpret_cast<uint64_t>(a.in) + a.in_off[m] - 16ull * b0;
       r.dst0 = reinterpret_cast<uint64_t>(a.out) + a.out_off[m] - 16ull * b0;
@@ -1017,7 +1030,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       // instead of one lane working through a whole schedule alone.
 #pragma unroll 1
       for (uint32_t j = 0; j < G; ++j) {
-        const uint32_t nr_j = __shfl_sync(0xffffffffu, dec_nr, j);
+        const uint32_t nr_j = __shfl_sync(0xffffffffu, nr, j);
         if (nr_j != 0 && lane / 4 <= nr_j / 2)
           decrypt_schedule_unit(T, sb, sb_off, nr_j, wrk + j * kShortStride<OPB>, lane / 4, lane % 4);
       }

@@ -185,17 +185,31 @@ def test_batch_schedule_table_matches_raw_keys(torch, B, oracle):
     tbits = W.key_sizes(70, n_tenants)
     table = b"".join(bytes(A.aes_expand_key(tkeys[t][: tbits[t] // 8], int(tbits[t]))) for t in range(n_tenants))
     sched = torch.frombuffer(bytearray(table), dtype=torch.uint8).cuda()
+    # both builds of the persistent kernel (1024 and 512 threads per CTA)
+    configs = (None, B.AesBatchConfig(512, 0, 0, 0))
     for op in (0, 1):
         b = build(B, torch, op, lengths, None, None, ivs if op == 0 else None, seed=13,
-                  schedules=sched, n_schedules=n_tenants, sched_idx=tid).submit()
-        torch.cuda.synchronize()
-        oracle_check(B, oracle, b, tbits[tid], tkeys[tid], ivs)
+                  schedules=sched, n_schedules=n_tenants, sched_idx=tid)
+        for cfg in configs:
+            b.out.fill_(0)
+            b.submit(config=cfg)
+            torch.cuda.synchronize()
+            oracle_check(B, oracle, b, tbits[tid], tkeys[tid], ivs)
     enc = b  # op 1 output: decrypt it through the schedule table too
     ct_len = enc.out_len.cpu().numpy().astype(np.uint64)
+    src = enc.data.cpu().numpy()
+    in_off = enc.in_off.cpu().numpy()
     dec = B.Batch(B.BATCH_ECB_PKCS7_DECRYPT, enc.out, enc.out_off_np, ct_len, schedules=sched,
-                  n_schedules=n_tenants, sched_idx=tid).submit()
-    torch.cuda.synchronize()
-    assert np.array_equal(dec.out_len.cpu().numpy(), lengths.astype(np.int64))
+                  n_schedules=n_tenants, sched_idx=tid)
+    for cfg in configs:
+        dec.out.fill_(0)
+        dec.submit(config=cfg)
+        torch.cuda.synchronize()
+        assert np.array_equal(dec.out_len.cpu().numpy(), lengths.astype(np.int64))
+        res = dec.out.cpu().numpy()
+        for m in range(n):
+            o, i, ln = int(dec.out_off_np[m]), int(in_off[m]), int(lengths[m])
+            assert np.array_equal(res[o: o + ln], src[i: i + ln]), (cfg, m)
 
 
 def test_batch_many_tiny_messages_multi_window(torch, B, oracle):
