@@ -264,15 +264,30 @@ aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
  * encrypted in parallel and the results concatenated into the output file).
  *
  * Here the chunks are fixed-size pieces of the file handed to `threads`
- * worker threads.  Each worker owns one pinned host buffer and one CUDA
- * stream and repeats: read its next chunk at the chunk's file offset, run the
- * cipher on the pinned buffer in place (the kernel reads and writes host
- * memory over the CPU-GPU link; no device copy), wait for that stream, copy
- * the chunk to the same offset of dst (through a shared mapping of dst, or
- * pwrite when dst cannot be mapped).  Reads, writes and GPU work of
- * different chunks overlap.  Another process truncating dst during the call
- * makes the mapped copy fault (SIGBUS), as with any mapped file.  CTR chunks use the IV whose 32-bit counter is
- * advanced by the chunk's first block (mod 2^32), so the output is
+ * worker threads, on one of two paths:
+ *  - direct (when the current device reads and writes pageable host memory
+ *    through the host's page tables, cudaDevAttrPageableMemoryAccess, as on
+ *    Grace-Blackwell over NVLink-C2C): both files are mapped and the kernel
+ *    reads the source chunk and writes the destination chunk in place in
+ *    the mappings, no host copy.  Each worker first faults in its chunk's
+ *    pages of both mappings, so the device never meets a missing page:
+ *    MADV_POPULATE_READ for src; for dst a store of 0 into each page's first
+ *    byte inside the chunk (bytes the kernel then overwrites), or, in place,
+ *    MADV_POPULATE_WRITE (one access per page on kernels without
+ *    MADV_POPULATE_*).  It then launches the cipher on its own stream and
+ *    takes the next chunk; each worker waits for its stream at the end.
+ *  - staged (otherwise, or with AES_FILE_STAGED): each worker owns one pinned
+ *    host buffer and one CUDA stream and repeats: read its next chunk at the
+ *    chunk's file offset, run the cipher on the pinned buffer in place (the
+ *    kernel reads and writes host memory over the CPU-GPU link; no device
+ *    copy), wait for that stream, copy the chunk to the same offset of dst
+ *    (through a shared mapping of dst, or pwrite when dst cannot be mapped).
+ * Reads, writes and GPU work of different chunks overlap.  Another process
+ * truncating src or dst during the call makes a mapped access fail (SIGBUS
+ * on the host; on the direct path a device access to a page gone from the
+ * mapping faults the CUDA context), as with any mapped file: the files must
+ * keep their length while the call runs.  CTR chunks use the IV whose 32-bit
+ * counter is advanced by the chunk's first block (mod 2^32), so the output is
  * byte-identical to one call on the whole file; ECB needs a file length that
  * is a multiple of 16 (no padding here).
  *
@@ -284,10 +299,10 @@ aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
  * Runs on the calling thread's current CUDA device and returns when dst is
  * complete (or on the first failure: AES_ERR_IO with stats->os_errno set,
  * AES_ERR_CUDA, AES_ERR_LENGTH for a ragged ECB file, AES_ERR_ARG for a bad
- * argument; dst is then incomplete).  Pinned memory: threads buffers of
- * chunk_bytes rounded up to whole MiB; the call returns them to a
- * process-wide pool (at most 64 buffers) that later calls reuse, since
- * pinning host memory costs about as much as a few GB of file traffic;
+ * argument; dst is then incomplete).  Pinned memory (staged path only):
+ * threads buffers of chunk_bytes rounded up to whole MiB; the call returns
+ * them to a process-wide pool (at most 64 buffers) that later calls reuse,
+ * since pinning host memory costs about as much as a few GB of file traffic;
  * aes_file_trim() frees the pool. */
 typedef enum aes_file_mode {
     AES_FILE_CTR = 0,
@@ -295,19 +310,23 @@ typedef enum aes_file_mode {
     AES_FILE_ECB_DECRYPT = 2
 } aes_file_mode;
 
+#define AES_FILE_STAGED 1u  /* take the staged path even where the direct one is possible */
+
 typedef struct aes_file_config {
-    uint64_t chunk_bytes;  /* bytes per chunk: a multiple of 16, 0 = 4 MiB */
+    uint64_t chunk_bytes;  /* bytes per chunk: a multiple of 16; 0 = 64 MiB direct, 4 MiB staged */
     int32_t threads;       /* worker threads, 1..64; 0 = min(16, hardware threads) */
-    int32_t reserved;      /* 0 */
+    uint32_t flags;        /* 0 or AES_FILE_STAGED; other bits: AES_ERR_ARG */
 } aes_file_config;
 
 typedef struct aes_file_stats {
     uint64_t bytes;         /* file length */
     uint64_t chunks;        /* chunks processed */
     double seconds;         /* wall time of the call */
-    double setup_seconds;   /* of which: pinned buffers and streams */
+    double setup_seconds;   /* of which: mappings, pinned buffers and streams */
     int32_t threads;        /* workers used */
     int32_t os_errno;       /* errno of the failing file operation (AES_ERR_IO), else 0 */
+    int32_t direct;         /* 1: the direct path ran, 0: the staged one */
+    int32_t reserved;       /* 0 */
 } aes_file_stats;
 
 aes_status aes_file_crypt(const char *src_path, const char *dst_path, aes_file_mode mode,

@@ -49,8 +49,27 @@ aes_status check_schedule(const aes_key_schedule* ks) {
   return ok ? AES_OK : AES_ERR_KEYSIZE;
 }
 
+// Whether the current device reads and writes pageable host memory
+// coherently through the host's page tables (cudaDevAttrPageableMemoryAccess,
+// as on Grace-Blackwell over NVLink-C2C), looked up once per device ordinal.
+bool pageable_access() {
+  static std::atomic<int> cache[64];  // 0 unknown, 1 no, 2 yes
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c != 0) return c == 2;
+  }
+  int v = 0;
+  const bool yes = cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess && v == 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(yes ? 2 : 1, std::memory_order_relaxed);
+  return yes;
+}
+
 // Resolve a caller pointer to one the current device can dereference.
-aes_status device_view(const void* p, const void** dev) {
+// Pageable host memory only with `pageable_ok` (the library's own file
+// mappings) on a device that reaches it through the host's page tables.
+aes_status device_view(const void* p, const void** dev, bool pageable_ok) {
   cudaPointerAttributes attr{};
   cudaError_t e = cudaPointerGetAttributes(&attr, p);
   if (e != cudaSuccess) return cuda_failure(e);
@@ -69,20 +88,25 @@ aes_status device_view(const void* p, const void** dev) {
       if (attr.devicePointer == nullptr) return AES_ERR_ARG;
       *dev = attr.devicePointer;
       return AES_OK;
-    default:  // pageable host memory is not accepted by these calls
+    default:  // pageable host memory: not accepted from callers
+      if (pageable_ok && attr.type == cudaMemoryTypeUnregistered && pageable_access()) {
+        *dev = p;
+        return AES_OK;
+      }
       return AES_ERR_ARG;
   }
 }
 
-aes_status check_buffers(const void* in, void* out, size_t nbytes, const void** din, void** dout) {
+aes_status check_buffers(const void* in, void* out, size_t nbytes, const void** din, void** dout,
+                         bool pageable_ok = false) {
   if (in == nullptr || out == nullptr) return AES_ERR_ARG;
   const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
   if ((a | b) & 15u) return AES_ERR_ALIGN;
   if (a != b && a < b + nbytes && b < a + nbytes) return AES_ERR_OVERLAP;
-  aes_status s = device_view(in, din);
+  aes_status s = device_view(in, din, pageable_ok);
   if (s != AES_OK) return s;
   const void* o = nullptr;
-  s = device_view(out, &o);
+  s = device_view(out, &o, pageable_ok);
   if (s != AES_OK) return s;
   *dout = const_cast<void*>(o);
   return AES_OK;
@@ -175,7 +199,7 @@ CtrParams make_ctr_params(const aes_key_schedule* ks, const uint8_t iv[16]) {
 }
 
 aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void* in, void* out,
-               size_t nbytes, void* stream, const aes_launch_config* cfg) {
+               size_t nbytes, void* stream, const aes_launch_config* cfg, bool pageable_ok = false) {
   aes_status s = check_schedule(ks);
   if (s != AES_OK) return s;
   if (op == Op::kCtr && iv == nullptr) return AES_ERR_ARG;
@@ -186,7 +210,7 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
   if (nbytes == 0) return AES_OK;
   const void* din = nullptr;
   void* dout = nullptr;
-  s = check_buffers(in, out, nbytes, &din, &dout);
+  s = check_buffers(in, out, nbytes, &din, &dout, pageable_ok);
   if (s != AES_OK) return s;
   const uint64_t nblocks = nbytes / 16;
   const uint32_t tail = static_cast<uint32_t>(nbytes % 16);
@@ -293,10 +317,10 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
   if (grid < 1) return AES_ERR_ARG;
   const void* din = nullptr;
   void* dout = nullptr;
-  aes_status st = device_view(b->in, &din);
+  aes_status st = device_view(b->in, &din, false);
   if (st != AES_OK) return st;
   const void* o = nullptr;
-  st = device_view(b->out, &o);
+  st = device_view(b->out, &o, false);
   if (st != AES_OK) return st;
   dout = const_cast<void*>(o);
   BatchArgs a{};
@@ -327,6 +351,17 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
 
 // Records a CUDA failure for aes_last_cuda_error() from other translation units.
 aes_status record_cuda_failure(cudaError_t e) { return cuda_failure(e); }
+
+// For aes_file_crypt's direct path: whether the current device can run the
+// cipher on mapped files, and the single-buffer cipher (mode as
+// aes_file_mode) on host memory the library mapped itself.
+bool host_pageable_access() { return pageable_access(); }
+
+aes_status crypt_mapped(int mode, const aes_key_schedule* ks, const uint8_t* iv, const void* in, void* out,
+                        size_t nbytes, cudaStream_t stream) {
+  const Op op = mode == AES_FILE_CTR ? Op::kCtr : mode == AES_FILE_ECB_ENCRYPT ? Op::kEcbEncrypt : Op::kEcbDecrypt;
+  return run(op, ks, iv, in, out, nbytes, stream, nullptr, true);
+}
 
 }  // namespace aesgpu
 

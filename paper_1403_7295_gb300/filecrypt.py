@@ -1,9 +1,11 @@
 """Encrypt or decrypt a file on the GPU: the paper's workload (a file in, the
 encrypted file out, §IV), through the library's native pipeline
-``aes_file_crypt`` (include/aesgpu.h): worker threads, each with one pinned
-chunk buffer and one CUDA stream, read a chunk at its file offset, run the
-cipher on the pinned buffer in place (the kernel reads and writes host memory
-over NVLink-C2C), and write the chunk at the same offset of the output.  CTR
+``aes_file_crypt`` (include/aesgpu.h).  Worker threads take fixed-size
+chunks.  Where the device reaches pageable host memory through the host's
+page tables (Grace-Blackwell over NVLink-C2C), both files are mapped and the
+kernel reads and writes the mapped chunks directly (the direct path, no host
+copy); otherwise each worker reads its chunk into a pinned buffer, runs the
+cipher on it in place and copies it into the output (the staged path).  CTR
 chunks use the IV advanced by the chunk's first block, so the result is
 byte-identical to one call on the whole file.  ECB needs a file length that
 is a multiple of 16 (no padding here).
@@ -23,13 +25,17 @@ from . import aes as _aes
 MODES = {"ctr": 0, "ecb-enc": 1, "ecb-dec": 2}
 
 
+STAGED = 1  # AES_FILE_STAGED: take the staged path even where the direct one is possible
+
+
 class FileConfig(ctypes.Structure):
-    _fields_ = [("chunk_bytes", ctypes.c_uint64), ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("chunk_bytes", ctypes.c_uint64), ("threads", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
 class FileStats(ctypes.Structure):
     _fields_ = [("bytes", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("seconds", ctypes.c_double),
-                ("setup_seconds", ctypes.c_double), ("threads", ctypes.c_int32), ("os_errno", ctypes.c_int32)]
+                ("setup_seconds", ctypes.c_double), ("threads", ctypes.c_int32), ("os_errno", ctypes.c_int32),
+                ("direct", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _declare():
@@ -45,12 +51,14 @@ def _declare():
     return L
 
 
-def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes: int = 4 << 20,
-               threads: int = 0) -> dict:
+def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes: int = 0,
+               threads: int = 0, staged: bool = False) -> dict:
     """Process `src` into `dst` (the same path encrypts in place); returns
-    bytes, chunks, seconds (of which setup), worker threads and GB/s file to
-    file.  Raises ValueError for a bad mode, IV or ragged ECB length, and
-    OSError / AesError when the native call fails."""
+    bytes, chunks, seconds (of which setup), worker threads, whether the
+    direct path ran, and GB/s file to file.  chunk_bytes 0 takes the path's
+    default (64 MiB direct, 4 MiB staged); `staged` forces the staged path.
+    Raises ValueError for a bad mode, IV or ragged ECB length, and OSError /
+    AesError when the native call fails."""
     if mode not in MODES:
         raise ValueError(f"unknown mode {mode}")
     if chunk_bytes % 16:
@@ -61,7 +69,7 @@ def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes:
         raise ValueError("ECB needs a file length that is a multiple of 16")
     ks = _aes.aes_expand_key(key)
     ivb = ctypes.create_string_buffer(bytes(iv), 16) if mode == "ctr" else None
-    cfg = FileConfig(chunk_bytes, threads, 0)
+    cfg = FileConfig(chunk_bytes, threads, STAGED if staged else 0)
     st = FileStats()
     rc = _declare().aes_file_crypt(os.fsencode(src), os.fsencode(dst), MODES[mode], ctypes.byref(ks),
                                    ivb, ctypes.byref(cfg), ctypes.byref(st))
@@ -69,12 +77,12 @@ def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes:
         raise OSError(st.os_errno, os.strerror(st.os_errno) if st.os_errno else "file I/O failed", src)
     _aes._check(rc, "aes_file_crypt")
     return {"bytes": st.bytes, "chunks": st.chunks, "seconds": st.seconds, "setup_seconds": st.setup_seconds,
-            "threads": st.threads, "chunk_bytes": chunk_bytes,
+            "threads": st.threads, "chunk_bytes": chunk_bytes, "direct": bool(st.direct),
             "gbps": st.bytes / st.seconds / 1e9 if st.seconds > 0 else 0.0}
 
 
 def trim() -> None:
-    """Free the pinned chunk buffers the pipeline keeps between calls."""
+    """Free the pinned chunk buffers the staged path keeps between calls."""
     _declare().aes_file_trim()
 
 
@@ -85,12 +93,13 @@ def main():
     p.add_argument("dst")
     p.add_argument("--key", required=True, help="hex, 16/24/32 bytes")
     p.add_argument("--iv", default=None, help="hex, 16 bytes (CTR)")
-    p.add_argument("--chunk-mib", type=int, default=4)
+    p.add_argument("--chunk-mib", type=int, default=0, help="0: the path's default")
     p.add_argument("--threads", type=int, default=0)
+    p.add_argument("--staged", action="store_true", help="pinned buffers even where the files could be mapped")
     a = p.parse_args()
     iv = bytes.fromhex(a.iv) if a.iv else None
     r = crypt_file(a.src, a.dst, np.frombuffer(bytes.fromhex(a.key), np.uint8), a.mode, iv,
-                   a.chunk_mib << 20, a.threads)
+                   a.chunk_mib << 20, a.threads, a.staged)
     print(r)
 
 

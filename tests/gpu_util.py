@@ -51,3 +51,20 @@ def library_mapped() -> bool:
     """True once libaesgpu.so is mapped into this process."""
     with open("/proc/self/maps") as f:
         return any("libaesgpu.so" in line for line in f)
+
+
+def pageable_memory_access():
+    """cudaDevAttrPageableMemoryAccess of device 0 from the CUDA runtime, or
+    None when no runtime library is found."""
+    import ctypes
+    import glob
+
+    libs = sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so*"))
+    if not libs:
+        return None
+    rt = ctypes.CDLL(libs[0])
+    v = ctypes.c_int(0)
+    if rt.cudaDeviceGetAttribute(ctypes.byref(v), 88, 0) != 0:  # 88: cudaDevAttrPageableMemoryAccess
+        return None
+    return v.value == 1
+

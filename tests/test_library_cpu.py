@@ -159,7 +159,7 @@ def test_file_crypt_validation_and_empty_file(lib, tmp_path):
     assert L.aes_file_crypt(s, d, 3, kr, ivb, None, None) == 1                     # unknown mode
     assert L.aes_file_crypt(s, d, 0, kr, None, None, None) == 1                    # CTR without IV
     assert L.aes_file_crypt(s, d, 0, None, ivb, None, None) == 1                   # no key
-    for cfg in (F.FileConfig(17, 0, 0), F.FileConfig(0, 65, 0), F.FileConfig(0, -1, 0), F.FileConfig(0, 0, 1)):
+    for cfg in (F.FileConfig(17, 0, 0), F.FileConfig(0, 65, 0), F.FileConfig(0, -1, 0), F.FileConfig(0, 0, 2)):
         assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(cfg), None) == 1
     missing = os.fsencode(tmp_path / "missing")
     assert L.aes_file_crypt(missing, d, 0, kr, ivb, None, ctypes.byref(st)) == 11
@@ -169,7 +169,9 @@ def test_file_crypt_validation_and_empty_file(lib, tmp_path):
     assert not dst.exists()
     src.write_bytes(b"")
     assert L.aes_file_crypt(s, d, 0, kr, ivb, None, ctypes.byref(st)) == 0
-    assert dst.exists() and dst.stat().st_size == 0 and st.bytes == 0 and st.chunks == 0
+    assert dst.exists() and dst.stat().st_size == 0 and st.bytes == 0 and st.chunks == 0 and st.direct == 0
+    staged = F.FileConfig(0, 0, F.STAGED)  # a known flag: accepted
+    assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(staged), None) == 0
     L.aes_file_trim()  # nothing pinned yet: a no-op without a GPU
 
 
