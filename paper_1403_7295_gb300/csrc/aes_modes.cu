@@ -192,7 +192,8 @@ cudaError_t launch_cbc(const void* in, void* out, uint64_t nblocks, const RoundK
   cudaError_t e = ensure_dynamic_smem(kern, kTtableSmemDec);
   if (e != cudaSuccess) return e;
   const uint64_t needed = (nblocks + shape.cta_threads - 1) / shape.cta_threads;
-  const uint64_t grid = shape.grid_ctas < needed ? shape.grid_ctas : (needed ? needed : 1);
+  const uint64_t ctas = static_cast<uint64_t>(shape.grid_ctas);  // positive: resolved by the caller
+  const uint64_t grid = ctas < needed ? ctas : (needed ? needed : 1);
   return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemDec, stream,
                     static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk, cp);
 }
@@ -208,7 +209,8 @@ cudaError_t launch_xts(const void* in, void* out, uint64_t nblocks, const RoundK
   const uint64_t groups = (nblocks / 32 + 31) / 32;
   const uint64_t warps_per_cta = shape.cta_threads / 32;
   const uint64_t needed = (groups + warps_per_cta - 1) / warps_per_cta;
-  const uint64_t grid = shape.grid_ctas < needed ? shape.grid_ctas : (needed ? needed : 1);
+  const uint64_t ctas = static_cast<uint64_t>(shape.grid_ctas);  // positive: resolved by the caller
+  const uint64_t grid = ctas < needed ? ctas : (needed ? needed : 1);
   return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, static_cast<size_t>(smem), stream,
                     static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, rk1, rk2, xp);
 }
