@@ -26,13 +26,13 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 
 
-# The batch kernel's translation unit holds six persistent-kernel builds (three
-# operations x two CTA sizes).  Its device code is optimised in parallel
-# pieces (build time 40 -> 15 s for that file).  Measured on GB300, the
-# 512-thread builds also come out faster (16,384 varlen messages: CTR 789
-# against 763 GB/s, ECB+PKCS#7 729 / 715 against 713 / 708), while the
-# 1024-thread short phase is 0.5-2.6 % slower.  Kept for the long messages.
-EXTRA_FLAGS = {"aes_batch.cu": ["-split-compile=4"]}
+# The batch kernel's 512-thread builds (aes_batch_regkeys.cu) have their
+# device code optimised in parallel pieces.  Measured on GB300, that flag also
+# gives them faster code (16,384 varlen messages: CTR 789 against 763 GB/s,
+# ECB+PKCS#7 729 / 715 against 713 / 708), while it costs the 1024-thread
+# builds (aes_batch.cu) 0.5-2.6 % on packet-sized messages, so they are
+# compiled without it.
+EXTRA_FLAGS = {"aes_batch_regkeys.cu": ["-split-compile=4"]}
 
 
 def nvcc() -> str:

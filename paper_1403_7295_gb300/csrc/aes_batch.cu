@@ -1152,11 +1152,12 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
   short_phase<OPB>(a, T, sb, sb_off, reinterpret_cast<char*>(rk_all), warp, lane);
 }
 
-template <int OPB>
-cudaError_t launch_persistent(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
+// The persistent kernel of one build (kRegKeys: the 512-thread one).
+template <int OPB, bool kRegKeys>
+cudaError_t launch_build(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
   constexpr size_t smem = batch_smem_bytes<OPB>();
   static_assert(smem + 64 <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
-  auto kern = cta <= 512 ? batch_kernel<OPB, true> : batch_kernel<OPB, false>;
+  auto kern = batch_kernel<OPB, kRegKeys>;
   cudaError_t e = ensure_dynamic_smem(kern, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<grid, cta, smem, s>>>(a);
@@ -1164,6 +1165,19 @@ cudaError_t launch_persistent(const BatchArgs& a, int cta, int grid, cudaStream_
 }
 
 }  // namespace
+
+#ifdef AES_BATCH_REGKEYS_TU
+// This translation unit (aes_batch_regkeys.cu) holds the 512-thread builds.
+cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
+  switch (a.op) {
+    case kBatchCtr: return launch_build<kBatchCtr, true>(a, cta, grid, s);
+    case kBatchEcbEnc: return launch_build<kBatchEcbEnc, true>(a, cta, grid, s);
+    case kBatchEcbDec: return launch_build<kBatchEcbDec, true>(a, cta, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+#else
+cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStream_t s);
 
 size_t batch_workspace_bytes(uint32_t n) {
   const size_t nchunks = (static_cast<size_t>(n) + kScanThreads * kScanItems - 1) /
@@ -1196,12 +1210,14 @@ cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s) 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (cta <= 512) return launch_batch_regkeys(a, cta, grid, s);
   switch (a.op) {
-    case kBatchCtr: return launch_persistent<kBatchCtr>(a, cta, grid, s);
-    case kBatchEcbEnc: return launch_persistent<kBatchEcbEnc>(a, cta, grid, s);
-    case kBatchEcbDec: return launch_persistent<kBatchEcbDec>(a, cta, grid, s);
+    case kBatchCtr: return launch_build<kBatchCtr, false>(a, cta, grid, s);
+    case kBatchEcbEnc: return launch_build<kBatchEcbEnc, false>(a, cta, grid, s);
+    case kBatchEcbDec: return launch_build<kBatchEcbDec, false>(a, cta, grid, s);
   }
   return cudaErrorInvalidValue;
 }
+#endif  // AES_BATCH_REGKEYS_TU
 
 }  // namespace aesgpu
