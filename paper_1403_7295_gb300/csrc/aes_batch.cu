@@ -160,6 +160,7 @@ __device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* sh,
   return before + x - v;
 }
 
+#ifndef AES_BATCH_REGKEYS_TU  // the scans run from aes_batch.cu's entry point only
 __global__ void __launch_bounds__(kScanThreads) batch_count_scan(const BatchArgs a) {
   __shared__ uint64_t sh[64];
   const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems +
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kScanThreads) batch_scan_fix(const BatchArgs a
     if (m < a.n) a.blk_off[m] += add;
   }
 }
+#endif  // AES_BATCH_REGKEYS_TU
 
 // ------------------------------------------------------------ persistent ----
 
