@@ -822,8 +822,9 @@ __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total, u
 // ------------------------------------------------------ short messages ----
 //
 // After the tile phase every warp works alone on groups of kGroup consecutive
-// messages.  A group's valid short messages are numbered in order (compact
-// index ci) and laid end to end in a group block space; lane l of a warp step
+// messages.  A group's valid short messages are numbered by round count,
+// then by position (compact index ci), and laid end to end in that order in
+// a group block space; lane l of a warp step
 // takes group block base + l.  The message of each lane's block follows from
 // one ballot (messages starting at or before `base`) and one OR-reduction (a
 // bit for every message starting inside the step), so there is no search.
@@ -948,13 +949,6 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       }
     }
     const uint32_t valid = __ballot_sync(0xffffffffu, nb > 0);
-    uint32_t incl = nb;  // inclusive prefix of the group's block counts
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= static_cast<uint32_t>(o)) incl += y;
-    }
-    const uint32_t nblk = __shfl_sync(0xffffffffu, incl, 31);
     uint32_t nr = 0;  // the lane's message's rounds (0: no message)
     const uint32_t* sched = nullptr;  // its resident schedule, copied below by the whole warp
     if (nb > 0) {
@@ -983,11 +977,25 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
         }
       }
     }
+    // The group's messages are laid end to end ordered by round count, then
+    // by lane (ci), so that a warp step mixes key sizes as rarely as the
+    // group allows: rounds 10-13 run masked, a step paying for its longest
+    // key.  b0 = blocks of the messages before this one in that order.
+    const uint32_t r10 = __ballot_sync(0xffffffffu, nr == 10), r12 = __ballot_sync(0xffffffffu, nr == 12);
+    const uint32_t r14 = valid & ~(r10 | r12);
+    const uint32_t lower = nr == 12 ? r10 : nr == 14 ? (r10 | r12) : 0u;
+    const uint32_t peers = nr == 10 ? r10 : nr == 12 ? r12 : r14;
+    const uint32_t ci = __popc(lower) + __popc(peers & ((1u << lane) - 1));
+    uint32_t b0 = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < G; ++j) {
+      const uint32_t nb_j = __shfl_sync(0xffffffffu, nb, j), ci_j = __shfl_sync(0xffffffffu, ci, j);
+      if (nb_j > 0 && ci_j < ci) b0 += nb_j;
+    }
+    const uint32_t nblk = __reduce_add_sync(0xffffffffu, nb);
     __syncwarp();
     if (nb > 0) {
       const uint32_t m = static_cast<uint32_t>(m0 + lane);
-      const uint32_t b0 = incl - nb;
-      const uint32_t ci = __popc(valid & ((1u << lane) - 1));
       uint32_t* rk = wrk + lane * kShortStride<OPB>;
       GroupMsg r;
       r.src0 = reinterpret_cast<uint64_t>(a.in) + a.in_off[m] - 16ull * b0;
@@ -1021,7 +1029,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       }
       r.info = nr | static_cast<uint32_t>(len & 15u) << 8 | lane << 16;
       r.full_end = b0 + static_cast<uint32_t>(len / 16);
-      r.end = incl;
+      r.end = b0 + nb;
       rec[ci] = r;
       first[ci] = b0;
     }
