@@ -17,12 +17,16 @@
 //      their keys on the device into shared memory (one thread per message,
 //      FIPS-197 §5.2; the equivalent inverse schedule for ECB decryption), and
 //      its warps run the T-table rounds of aes_ttable.cuh with round keys read
-//      from shared memory (one 128-bit broadcast load per round).  Short
-//      messages (1 .. kShortMax-1 blocks), afterwards: every warp on its own
-//      claims groups of consecutive messages, expands their keys into its own
-//      slots and runs their blocks, with no CTA barrier (so key expansion and
-//      claims of one warp overlap the rounds of the others, and the phase fills
-//      the tail of the tile phase).
+//      from shared memory (one 128-bit broadcast load per round) or, in the
+//      512-thread build, held in registers across a span.  Short messages
+//      (1 .. kShortMax-1 blocks), afterwards: every warp on its own claims
+//      groups of consecutive messages, expands their keys into its own slots
+//      and runs their blocks, with no CTA barrier (so key expansion and claims
+//      of one warp overlap the rounds of the others, and the phase fills the
+//      tail of the tile phase).
+//
+// The 1024-thread builds are compiled here; the 512-thread builds in
+// aes_batch_regkeys.cu, which includes this file with AES_BATCH_REGKEYS_TU.
 #include "aes_batch.h"
 #include "aes_smem_attr.h"
 #include "aes_ttable.cuh"
