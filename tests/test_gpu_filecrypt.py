@@ -102,3 +102,23 @@ def test_ecb_file_round_trip(torch, oracle, staged):
         open(src, "ab").write(b"x")
         with pytest.raises(ValueError):
             crypt_file(src, enc, key, "ecb-enc")
+
+
+@PATHS
+def test_existing_longer_destination_is_replaced(torch, oracle, staged):
+    """dst already holds other, longer content: afterwards it has exactly the
+    source length and the cipher bytes (nothing stale past the end, nothing
+    stale inside), on both paths."""
+    from paper_1403_7295_gb300.filecrypt import crypt_file
+
+    n = (5 << 20) + 333
+    data = synth.bytes_np(75, synth.STREAM_DATA, n)
+    key = synth.key_bytes(75, 256)
+    iv = synth.iv_bytes(75, counter0=0x7FFFFFF0)
+    with tempfile.TemporaryDirectory() as d:
+        src, enc = os.path.join(d, "p"), os.path.join(d, "c")
+        data.tofile(src)
+        synth.bytes_np(76, synth.STREAM_DATA, 2 * n + 4096).tofile(enc)
+        r = crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=(1 << 20) + 16, threads=6, staged=staged)
+        assert r["bytes"] == n and os.path.getsize(enc) == n
+        assert np.array_equal(np.fromfile(enc, np.uint8), oracle.ctr_xcrypt(key, 256, iv, data))
