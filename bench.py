@@ -51,12 +51,12 @@ def parse_args():
     p.add_argument("--bits", type=int, default=128, choices=[128, 192, 256])
     p.add_argument("--mode", default="ctr", choices=["ctr", "ecb_enc", "ecb_dec"])
     p.add_argument("--size-mib", type=int, default=1024)
-    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--variant", type=int, default=0, help="0 auto, 1 T-table, 2 bitsliced")
     p.add_argument("--cta", type=int, default=0)
     p.add_argument("--bpt", type=int, default=0)
     p.add_argument("--sweep", action="store_true", help="also time the 36-run key/mode/size sweep")
     p.add_argument("--file-pipeline", action="store_true",
-                   help="also time file -> encrypted file through the pinned-buffer pipeline (4 GiB)")
+                   help="also time file -> encrypted file (4 GiB in /dev/shm), direct (mapped files) and staged paths")
     p.add_argument("--scaling", action="store_true",
                    help="also time throughput vs buffer size and vs CTAs (the paper's Figs. 4-9 on GPU)")
     p.add_argument("--no-e2e", action="store_true")
