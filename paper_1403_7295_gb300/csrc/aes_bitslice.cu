@@ -258,24 +258,41 @@ __global__ void __launch_bounds__(kBsThreads)
     }
 
     to_slices(st);  // the transpose is its own inverse: back to column words
+    if constexpr (OP == Op::kCtr) {
+      // The data to XOR: eight blocks' loads issued together, then their
+      // stores (in and out may be the same buffer, so a load cannot move
+      // above an earlier store; one at a time would wait a memory round
+      // trip per block).
 #pragma unroll
-    for (int k = 0; k < kBlocksPerThread; ++k) {
-      const uint64_t idx = base + 32ull * k;
-      const uint4 r = make_uint4(st[k], st[32 + k], st[16 + k], st[48 + k]);
-      if constexpr (OP == Op::kCtr) {
-        if (idx < nblocks) {
-          const uint4 v = __ldcs(in + idx);
-          __stcs(out + idx, make_uint4(v.x ^ r.x, v.y ^ r.y, v.z ^ r.z, v.w ^ r.w));
-        } else if (idx == nblocks && tail_bytes) {  // partial last block
-          const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
-          uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
-          for (uint32_t b = 0; b < tail_bytes; ++b) {
-            const uint32_t w = b < 4 ? r.x : b < 8 ? r.y : b < 12 ? r.z : r.w;
-            dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
+      for (int g = 0; g < kBlocksPerThread; g += 8) {
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint64_t idx = base + 32ull * (g + j);
+          v[j] = idx < nblocks ? __ldcs(in + idx) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = g + j;
+          const uint64_t idx = base + 32ull * k;
+          const uint4 r = make_uint4(st[k], st[32 + k], st[16 + k], st[48 + k]);
+          if (idx < nblocks) {
+            __stcs(out + idx, make_uint4(v[j].x ^ r.x, v[j].y ^ r.y, v[j].z ^ r.z, v[j].w ^ r.w));
+          } else if (idx == nblocks && tail_bytes) {  // partial last block
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(in + nblocks);
+            uint8_t* dst = reinterpret_cast<uint8_t*>(out + nblocks);
+            for (uint32_t b = 0; b < tail_bytes; ++b) {
+              const uint32_t w = b < 4 ? r.x : b < 8 ? r.y : b < 12 ? r.z : r.w;
+              dst[b] = src[b] ^ static_cast<uint8_t>(w >> (8 * (b & 3)));
+            }
           }
         }
-      } else {
-        if (idx < nblocks) __stcs(out + idx, r);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kBlocksPerThread; ++k) {
+        const uint64_t idx = base + 32ull * k;
+        if (idx < nblocks) __stcs(out + idx, make_uint4(st[k], st[32 + k], st[16 + k], st[48 + k]));
       }
     }
   }
