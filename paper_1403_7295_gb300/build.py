@@ -26,13 +26,11 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 
 
-# The batch kernel's 512-thread builds (aes_batch_regkeys.cu) have their
-# device code optimised in parallel pieces.  Measured on GB300, that flag also
-# gives them faster code (16,384 varlen messages: CTR 789 against 763 GB/s,
-# ECB+PKCS#7 729 / 715 against 713 / 708), while it costs the 1024-thread
-# builds (aes_batch.cu) 0.5-2.6 % on packet-sized messages, so they are
-# compiled without it.
-EXTRA_FLAGS = {"aes_batch_regkeys.cu": ["-split-compile=4"]}
+# Per-file extra nvcc flags (none at present).  nvcc's -split-compile was
+# tried on the batch kernel and dropped: its output is not deterministic
+# (the same source compiled five times gave two different register
+# allocations), so it cannot be measured once and relied on.
+EXTRA_FLAGS: dict[str, list[str]] = {}
 
 
 def nvcc() -> str:
