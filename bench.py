@@ -1,10 +1,10 @@
 #!/usr/bin/env python3
 """Throughput bench for GB300 bulk AES (one JSON line on rank 0).
 
-Default workload: AES-128 CTR encryption of one 1 GiB buffer of seeded
-uniform random bytes (the single-large-buffer case of the size sweep), data
-resident in HBM, one library call per step.  The input is larger than L2
-(129 MB), so no L2 flush is needed between steps.
+Default workload: AES-128 CTR encryption of one 8 GiB buffer of seeded
+uniform random bytes (the largest buffer of the single-buffer sweep, 64 MiB /
+1 GiB / 8 GiB), data resident in HBM, one library call per step.  The input
+is larger than L2 (129 MB), so no L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                   [--bits 128|192|256] [--mode ctr|ecb_enc|ecb_dec] [--size-mib M]
@@ -45,20 +45,21 @@ HBM_FALLBACK_GBPS = 6800.0
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
-    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     p.add_argument("--bits", type=int, default=128, choices=[128, 192, 256])
     p.add_argument("--mode", default="ctr", choices=["ctr", "ecb_enc", "ecb_dec"])
-    p.add_argument("--size-mib", type=int, default=1024)
+    p.add_argument("--size-mib", type=int, default=8192)
     p.add_argument("--variant", type=int, default=0, help="0 auto, 1 T-table, 2 bitsliced")
     p.add_argument("--cta", type=int, default=0)
     p.add_argument("--bpt", type=int, default=0)
     p.add_argument("--sweep", action="store_true", help="also time the 36-run key/mode/size sweep")
     p.add_argument("--file-pipeline", action="store_true",
                    help="also time file -> encrypted file (4 GiB in /dev/shm), direct (mapped files) and staged paths")
-    p.add_argument("--scaling", action="store_true",
-                   help="also time throughput vs buffer size and vs CTAs (the paper's Figs. 4-9 on GPU)")
+    p.add_argument("--no-scaling", action="store_true",
+                   help="skip the compact scaling study (throughput vs buffer size and vs CTAs, the paper's "
+                        "Figs. 4-9 on GPU, plus the CTR size sweep at 64 MiB / 1 GiB / 8 GiB)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-probes", action="store_true")
@@ -68,8 +69,11 @@ def parse_args():
                    help="'batched': time only the batched varlen workload; 'small': only the "
                         "1,000,000 packet-sized messages (profiling entries)")
     p.add_argument("--batch-msgs", type=int, default=16384, help="messages in the batched varlen workload")
-    p.add_argument("--serve-seconds", type=float, default=10.0,
-                   help="duration of the serving leg (Poisson 50k req/s); 0 skips it")
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="duration of the serving leg (Poisson 50k req/s, the configured 60 s); 0 skips it "
+                        "and the loaded point")
+    p.add_argument("--serve-loaded-seconds", type=float, default=10.0,
+                   help="duration of the loaded serving point (Poisson 250k req/s, 1 GiB budget); 0 skips it")
     return p.parse_args()
 
 
@@ -100,16 +104,19 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id: str):
+    def __init__(self, gpu_id: str, period_ms: int = 25):
         self.gpu_id = gpu_id
+        self.period_ms = period_ms
         self.proc = None
         self.lines: list[str] = []
+        self.stamps: list[float] = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                 "-lms", str(self.period_ms), "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
                 text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -119,6 +126,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
+            self.stamps.append(time.perf_counter())
             self.lines.append(line.strip())
 
     def stop(self) -> dict:
@@ -130,9 +138,18 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self._t.join(timeout=2)
+        return self.summary()
+
+    def summary(self, t0: float | None = None, t1: float | None = None) -> dict:
+        """Median SM clock, max clock, power and throttle reasons of the
+        samples read between perf_counter times t0 and t1 (all if None)."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in zip(list(self.stamps), list(self.lines)):
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -259,11 +276,10 @@ def gpu_arm(args):
     seed = rank
     bits = args.bits
     # Every rank holds one shard of a logical world x size buffer under one key:
-    # rank r's counter starts at its first block (the paper's chunk split, no exchange).
-    from paper_1403_7295_gb300.shard import ctr_iv_at
-
+    # rank r's counter starts at its first block (the paper's chunk split, no
+    # exchange); the library's aes_ctr_iv_advance gives that IV.
     key = synth.key_bytes(0, bits)
-    iv = np.frombuffer(ctr_iv_at(synth.iv_bytes(0), rank * (nbytes // 16)), np.uint8)
+    iv = np.frombuffer(A.aes_ctr_iv_advance(synth.iv_bytes(0), rank * (nbytes // 16)), np.uint8)
     ks = A.aes_expand_key(key)
     x = synth.bytes_torch(seed, synth.STREAM_DATA, nbytes, device="cuda")
     y = torch.empty_like(x)
@@ -285,7 +301,7 @@ def gpu_arm(args):
         sampler.start()
     ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), args.steps, args.warmup,
                      barrier)
-    clocks = sampler.stop() if sampler else None
+    clocks = sampler.summary() if sampler else None
     dist_steps = per_step_stats(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), min(args.steps, 200))
     t = torch.tensor([ms], device="cuda")
     if dist:
@@ -309,7 +325,8 @@ def gpu_arm(args):
         "data": "synthetic: SplitMix64-seeded uniform random bytes",
         "config": {
             "workload": f"AES-{bits} {args.mode.upper()} of one {args.size_mib} MiB buffer per GPU, "
-                        "device-resident (single-buffer sweep, largest-buffer headline case)",
+                        "device-resident (single-buffer sweep 64 MiB / 1 GiB / 8 GiB; "
+                        + ("its largest buffer)" if args.size_mib == 8192 else "not its largest buffer)"),
             "key_bits": bits, "mode": args.mode, "buffer_bytes": nbytes,
             "l2": "input larger than L2 (129 MB); no flush",
             "launch": cfg or "library default",
@@ -320,43 +337,8 @@ def gpu_arm(args):
     }
     if rank == 0:
         blocks = nbytes / 16
-        clock_mhz = sm_max_mhz
-        hbm = {"hbm_gbps_moved": round(2 * nbytes / per_launch_s / 1e9, 1),
-               "hbm_peak_gbps": hbm_peak, "hbm_frac": round(2 * nbytes / per_launch_s / 1e9 / hbm_peak, 4),
-               "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json copy bandwidth)" if peak_src == "measured"
-               else "fallback 6.8 TB/s"}
-        if args.variant == 2:
-            # bitsliced rounds: no lookups; bound by the ALU pipe (LOP3 / PRMT / SHF)
-            ops = read_profile_field(args, "thread_instructions_per_block_measured:")
-            rl = {"bound": "alu", "unit": "Gop/s", "achieved": None, "peak": None, "frac": None,
-                  "traffic": read_traffic(args), "ops_per_block": ops,
-                  "pipe": "64-lane ALU pipe (LOP3, PRMT, SHF of the bitsliced circuit)", **hbm}
-            if ops and probes and probes.get("lop3"):
-                peak = probes["lop3"] * sms * clock_mhz * 1e6 / 1e9
-                rl["achieved"] = round(ops * blocks / per_launch_s / 1e9, 1)
-                rl["peak"] = round(peak, 1)
-                rl["frac"] = round(rl["achieved"] / peak, 4)
-                rl["peak_source"] = (f"measured probe: {probes['lop3']} LOP3 per clock per SM x {sms} SMs "
-                                     f"x {clock_mhz:.0f} MHz (max SM clock)")
-        else:
-            lk = lookups_per_block(bits) * blocks
-            g_lookups = lk / per_launch_s / 1e9
-            rl = {"bound": "alu", "unit": "Glookup/s", "achieved": round(g_lookups, 1),
-                  "peak": None, "frac": None, "traffic": read_traffic(args),
-                  "ops_per_block": lookups_per_block(bits),
-                  "pipe": "32-bit shared-memory loads (replicated T-table lookups)", **hbm}
-            if probes and probes.get("lds32"):
-                peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
-                rl["peak"] = round(peak, 1)
-                rl["frac"] = round(g_lookups / peak, 4)
-                measured = read_profile_field(args, "lookups_per_block_measured:")
-                if measured:
-                    # the kernel's own lookups (CTR caching does fewer than 16*Nr): how busy the pipe is
-                    rl["lookups_per_block_measured"] = measured
-                    rl["pipe_frac"] = round(measured * blocks / per_launch_s / 1e9 / peak, 4)
-                rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM "
-                                     f"x {sms} SMs x {clock_mhz:.0f} MHz (max SM clock)")
-        result["roofline"] = rl
+        result["roofline"] = roofline(args, bits, nbytes, per_launch_s, probes, sms, sm_max_mhz,
+                                      hbm_peak, peak_src)
         dist_steps["gbps_at_median"] = round(nbytes / (dist_steps["median_ms"] / 1e3) / 1e9, 2)
         dist_steps["how"] = ("one event pair per launch, after the timed region (rank 0); the timed "
                              "value above is the event span over all steps")
@@ -365,34 +347,130 @@ def gpu_arm(args):
         result["clocks"] = clocks
         result["context"] = {"paper_best_cpu_gbps": round(PAPER_BEST_GBPS, 3),
                              "paper_best_cpu": "6637 Mb/s, pthreads, 4x Xeon X7560 (Table I)"}
-        if not args.no_e2e:
-            result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
+        del blocks
         if not args.no_variants:
             result["variants"] = variant_arm(torch, A, args, ks, iv, x, y, value)
-            result["other_modes"] = modes_arm(torch, A, x, y)
+            result["other_modes"] = modes_arm(torch, A, x[: 1 << 30], y[: 1 << 30])
+        if not args.no_scaling:
+            result["scaling_study"] = scaling_study(torch, A, x, y, sampler)
+        if sampler:
+            sampler.stop()
         if args.sweep:
             result["sweep"] = sweep(torch, A)
-        if args.scaling:
-            result["scaling_study"] = scaling_study(torch, A)
         if args.file_pipeline:
             result["file_pipeline"] = file_pipeline(torch)
+        del x, y
+        torch.cuda.empty_cache()
+        x = y = None
+        if not args.no_e2e:
+            result["e2e"] = e2e_arm(torch, A, args, ks, iv, nbytes, cfg)
         if not args.no_batch:
-            del x, y
-            torch.cuda.empty_cache()
-            x = y = None
-            result["batched"] = batched_arm(torch, A, value if world == 1 else None)
+            result["batched"] = batched_arm(torch, A)
         if args.serve_seconds > 0:
-            x = y = None
             torch.cuda.empty_cache()
             result["serving"] = serving_arm(torch, args.serve_seconds)
-        del x, y
+            if args.serve_loaded_seconds > 0:
+                result["serving_loaded"] = serving_arm(torch, args.serve_loaded_seconds, rate=250_000.0,
+                                                       budget_bytes=1 << 30)
         torch.cuda.empty_cache()
         if not args.no_cpu:
             result["cpu_baseline"] = cpu_baseline(args.bits, args.mode, budget_s=10.0)
         print(json.dumps(result), flush=True)
+    else:
+        del x, y
+        torch.cuda.empty_cache()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def roofline(args, bits, nbytes, per_launch_s, probes, sms, clock_mhz, hbm_peak, peak_src):
+    """The headline kernel against its three ceilings, each as GB/s of
+    plaintext: HBM (2 bytes moved per plaintext byte at the measured copy
+    bandwidth), the shared-memory pipe (the kernel's executed table lookups
+    per block at the probe's conflict-free LDS.32 rate) and the integer ALU
+    pipe (the kernel's ALU thread-instructions per block, from its ncu
+    summary, at the probe's LOP3 rate: the INT32 term).  The roofline is the
+    slowest of the three; `achieved`/`peak`/`frac` are the binding
+    shared-memory pipe's executed lookups per second against its peak."""
+    blocks = nbytes / 16
+    nr = {128: 10, 192: 12, 256: 14}[bits]
+    value_gbps = nbytes / per_launch_s / 1e9
+    hbm_ceiling = hbm_peak / 2
+    rl = {"hbm_gbps_moved": round(2 * nbytes / per_launch_s / 1e9, 1), "hbm_peak_gbps": hbm_peak,
+          "hbm_frac": round(2 * value_gbps / hbm_peak, 4),
+          "hbm_peak_source": f"{peak_src} (MEASURED_PEAKS.json copy bandwidth)" if peak_src == "measured"
+          else "fallback 6.8 TB/s", "traffic": read_traffic(args)}
+    if args.variant == 2:
+        # bitsliced rounds: no lookups; bound by the ALU pipe (LOP3 / PRMT / SHF)
+        ops = read_profile_field(args, "thread_instructions_per_block_measured:")
+        rl.update({"bound": "alu", "unit": "Gop/s", "achieved": None, "peak": None, "frac": None,
+                   "ops_per_block": ops, "pipe": "64-lane ALU pipe (LOP3, PRMT, SHF of the bitsliced circuit)"})
+        if ops and probes and probes.get("lop3"):
+            peak = probes["lop3"] * sms * clock_mhz * 1e6 / 1e9
+            rl["achieved"] = round(ops * blocks / per_launch_s / 1e9, 1)
+            rl["peak"] = round(peak, 1)
+            rl["frac"] = round(rl["achieved"] / peak, 4)
+            rl["peak_source"] = (f"measured probe: {probes['lop3']} LOP3 per clock per SM x {sms} SMs "
+                                 f"x {clock_mhz:.0f} MHz (max SM clock), of measured")
+        return rl
+    lk = read_profile_field(args, "lookups_per_block_measured:")
+    lk_src = "ncu (committed summary of this kernel source)"
+    if lk is None:
+        lk = executed_lookups_per_block(args, bits, nbytes)
+        lk_src = "the kernel's own lookup count, derived from its structure (no current ncu summary)"
+    alu = read_profile_field(args, "alu_instructions_per_block_measured:")
+    rl.update({"bound": "alu", "unit": "Glookup/s", "achieved": None, "peak": None, "frac": None,
+               "pipe": "shared-memory (LSU) pipe: replicated T-table lookups, 32-bit conflict-free",
+               "lookups_per_block_executed": lk, "lookups_source": lk_src,
+               "analytic_ops_per_block": 16 * nr,
+               "analytic_ops": "one table lookup per state byte per round (paper Fig. 1: SubBytes over "
+                               "16 bytes in each of Nr rounds) = 16*Nr; the run-cached CTR kernel executes fewer"})
+    terms = {"hbm": round(hbm_ceiling, 1)}
+    if probes and probes.get("lds32") and lk:
+        peak = probes["lds32"] * sms * clock_mhz * 1e6 / 1e9
+        rl["achieved"] = round(lk * blocks / per_launch_s / 1e9, 1)
+        rl["peak"] = round(peak, 1)
+        rl["frac"] = round(rl["achieved"] / peak, 4)
+        rl["achieved_analytic"] = round(16 * nr * blocks / per_launch_s / 1e9, 1)
+        rl["peak_source"] = (f"measured probe: {probes['lds32']} conflict-free LDS.32 per clock per SM x {sms} "
+                             f"SMs x {clock_mhz:.0f} MHz (max SM clock), of measured")
+        terms["lds"] = round(peak * 1e9 / lk * 16 / 1e9, 1)
+    if probes and probes.get("lop3") and alu:
+        ipeak = probes["lop3"] * sms * clock_mhz * 1e6 / 1e9
+        rl["int32"] = {"alu_instructions_per_block": alu, "unit": "Gop/s",
+                       "achieved": round(alu * blocks / per_launch_s / 1e9, 1), "peak": round(ipeak, 1),
+                       "frac": round(alu * blocks / per_launch_s / 1e9 / ipeak, 4),
+                       "peak_source": f"measured probe: {probes['lop3']} LOP3 per clock per SM (the 64-lane "
+                                      f"integer ALU pipe that LOP3, PRMT and SHF share) x {sms} SMs x "
+                                      f"{clock_mhz:.0f} MHz, of measured",
+                       "count_source": "ncu sm__inst_executed_pipe_alu of the committed summary"}
+        terms["alu"] = round(ipeak * 1e9 / alu * 16 / 1e9, 1)
+    rl["ceilings_gbps_plaintext"] = terms
+    binding = min(terms, key=terms.get)
+    rl["binding"] = binding
+    rl["roofline_gbps_plaintext"] = terms[binding]
+    rl["frac_of_roofline"] = round(value_gbps / terms[binding], 4)
+    return rl
+
+
+def executed_lookups_per_block(args, bits, nbytes):
+    """Table lookups the default CTR kernel executes per block, from its
+    structure: 16 per full round from round 3 on and in the final round, 5
+    for rounds 1-2 (the counter byte's round-1 lookup and its four round-2
+    lookups), and 15 per counter-run piece for the run's constants.  Other
+    modes and launch shapes execute the full 16*Nr."""
+    nr = {128: 10, 192: 12, 256: 14}[bits]
+    if args.mode != "ctr" or args.bpt or args.variant not in (0, 1):
+        return 16 * nr
+    units = nbytes // 16 + (1 if nbytes % 16 else 0)
+    runs = (units + 255) // 256
+    warps = 152 * 32
+    whole = runs - runs % warps
+    tail = runs - whole
+    pieces = whole + tail * (8 if tail and warps // tail >= 8 else 4 if tail and warps // tail >= 4
+                             else 2 if tail and warps // tail >= 2 else 1)
+    return round(16 * (nr - 2) + 5 + 15 * pieces / (nbytes / 16), 3)
 
 
 # The committed ncu summary of each round implementation's AES-128 CTR kernel,
@@ -470,7 +548,7 @@ def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):
     h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
     h_in.copy_(synth.bytes_torch(0, synth.STREAM_DATA, nbytes, device="cuda").cpu())
     h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-    steps = max(3, min(50, args.steps // 20))
+    steps = max(20, min(50, args.steps // 5))
     ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, h_in, h_out, cfg), steps, 3)
     val = nbytes * steps / (ms / 1e3) / 1e9
     # The ceiling: the host link moving the same bytes both ways at once
@@ -493,7 +571,7 @@ def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):
     # the link's capacity: best of three short samples (one sample can land on a
     # disturbed moment of the host's memory system)
     link = max(nbytes * 5 / (time_device(torch, both_ways, 5, 2) / 1e3) / 1e9 for _ in range(3))
-    del d_a, d_b
+    del d_a, d_b, h_in, h_out
     return {"value": round(val, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "steps": steps,
             "how": "aes call on pinned host input/output buffers (the kernel reads and writes host "
@@ -534,7 +612,7 @@ def batched_only(args):
                       "gbps": round(gbps, 1), "ms_per_batch": round(ms / args.steps, 3)}), flush=True)
 
 
-def batched_arm(torch, A, ctr128_gbps):
+def batched_arm(torch, A):
     """Batched workloads: (a) 16,384 messages, log-uniform 64 B .. 4 MiB, mixed
     key sizes, CTR, one persistent launch in a CUDA graph with an autotuned
     shape, against the byte-weighted harmonic mix of single-buffer 1 GiB CTR
@@ -544,15 +622,12 @@ def batched_arm(torch, A, ctr128_gbps):
     from synth import workloads as W
 
     out = {}
-    # single-buffer 1 GiB CTR rates per key size (128 from the headline run)
+    # single-buffer 1 GiB CTR rates per key size, measured here beside the batches
     rates = {}
     n = 1 << 30
     x = synth.bytes_torch(7, synth.STREAM_DATA, n, device="cuda")
     y = torch.empty_like(x)
     for bits in (128, 192, 256):
-        if bits == 128 and ctr128_gbps:
-            rates[bits] = ctr128_gbps
-            continue
         ks = A.aes_expand_key(synth.key_bytes(7, bits))
         iv = synth.iv_bytes(7)
         ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y), 100, 5)
@@ -635,8 +710,11 @@ def batched_arm(torch, A, ctr128_gbps):
                  sched_idx=np.arange(b.n, dtype=np.uint32), ivs=wl["ivs"], out=b.out)
     b2.capture(cfg)
     ms_pre = time_graph(torch, b2, steps)
+    g_dev = nbytes * steps / (ms_dev / 1e3) / 1e9
     out["small_1M"] = {
-        "gbps_device_key_expansion": round(nbytes * steps / (ms_dev / 1e3) / 1e9, 1),
+        "gbps_device_key_expansion": round(g_dev, 1),
+        "single_buffer_ctr128_1GiB_gbps": round(rates[128], 1),
+        "ratio_vs_single_buffer": round(g_dev / rates[128], 4),
         "gbps_preexpanded": round(nbytes * steps / (ms_pre / 1e3) / 1e9, 1),
         "bytes": nbytes, "ms_per_batch_device_keys": round(ms_dev / steps, 3),
         "ms_per_batch_preexpanded": round(ms_pre / steps, 3),
@@ -646,11 +724,12 @@ def batched_arm(torch, A, ctr128_gbps):
     return out
 
 
-def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
+def serving_arm(torch, seconds: float, rate: float = 50_000.0, budget_bytes: int = 8 << 30) -> dict:
     """Continuous-batching server: Poisson arrivals at `rate`/s for `seconds`,
     sizes 70 % 1-16 KiB / 25 % 16 KiB-1 MiB / 5 % 1-64 MiB, AES-256 CTR with
-    1,024 resident tenant schedules, 8 GiB admission budget, inputs sliced
-    from a 2 GiB device pool; p50/p99 of arrival -> completion."""
+    1,024 resident tenant schedules, admission under `budget_bytes` (the
+    configured 8 GiB by default), inputs sliced from a 2 GiB device pool;
+    p50/p99 of arrival -> completion."""
     from paper_1403_7295_gb300.serve import Server
     from synth import workloads as W
 
@@ -666,14 +745,15 @@ def serving_arm(torch, seconds: float, rate: float = 50_000.0) -> dict:
     u = synth.uniform01(5, synth.STREAM_MISC + 3, n)
     offs = (np.floor(u * (pool_bytes - lengths.astype(np.float64))).astype(np.uint64) // 16) * 16
     tenants = W.tenants(5, n, n_t)
-    srv = Server(pool, keys, bits, nonces, budget_bytes=8 << 30, n_streams=2, slots_per_stream=2,
+    srv = Server(pool, keys, bits, nonces, budget_bytes=budget_bytes, n_streams=2, slots_per_stream=2,
                  max_batch_msgs=8192)
     rep = srv.run(arr, tenants, offs, lengths, time_limit=seconds + 120.0)
     rep.pop("counters", None)
     rep["engine"] = "native aes_server_replay (admission, batching, launch and completion in the library)"
     rep.update({"rate_per_s": rate, "seconds": seconds, "key_bits": 256, "tenants": n_t,
-                "budget_bytes": 8 << 30, "offered_gbps": float(lengths.sum()) / seconds / 1e9})
-    for k in ("p50_ms", "p99_ms", "max_ms", "gbps", "wall_s", "mean_batch_msgs", "offered_gbps"):
+                "budget_bytes": budget_bytes, "offered_gbps": float(lengths.sum()) / seconds / 1e9})
+    for k in ("p50_ms", "p99_ms", "max_ms", "gbps", "wall_s", "mean_batch_msgs", "offered_gbps",
+              "admission_wait_p99_ms", "admission_wait_mean_ms", "admission_wait_max_ms"):
         if rep.get(k) is not None:
             rep[k] = round(rep[k], 3)
     srv.close()
@@ -697,54 +777,71 @@ def file_pipeline(torch, nbytes: int = 4 << 30) -> dict:
         x.cpu().numpy().tofile(src)
         del x
         key, iv = synth.key_bytes(12, 128), bytes(synth.iv_bytes(12))
-        cold = crypt_file(src, dst, key, "ctr", iv)
+        cold = crypt_file(src, dst, key, "ctr", iv)  # the default path: staged (pins its buffers)
         r = crypt_file(src, dst, key, "ctr", iv)
         r["where"] = base or tempfile.gettempdir()
         r["first_call_gbps"] = round(cold["gbps"], 3)
         r["first_call_setup_seconds"] = round(cold["setup_seconds"], 4)
         for k in ("seconds", "gbps", "setup_seconds"):
             r[k] = round(r[k], 4)
-        r["how"] = ("native aes_file_crypt, second call on the same files: " +
-                    ("direct path: both files mapped, workers fault in each chunk's pages and the kernel reads "
-                     "and writes the mappings over NVLink-C2C (no host copy)" if r["direct"] else
-                     "staged path: workers pread chunks into pinned buffers, the kernel encrypts them in place "
-                     "over NVLink-C2C, the chunks are copied into a shared mapping of the output file"))
-        crypt_file(src, dst, key, "ctr", iv, staged=True)  # pins the staged path's buffers
-        st = crypt_file(src, dst, key, "ctr", iv, staged=True)
-        r["staged_gbps"] = round(st["gbps"], 3)
-        r["staged_how"] = ("pread into pinned buffers, kernel in place over NVLink-C2C, copy into a shared "
-                           "mapping of the output (pinned buffers reused)")
+        r["how"] = ("native aes_file_crypt, default (staged) path, second call on the same files: workers "
+                    "pread chunks into pinned buffers, the kernel encrypts them in place over NVLink-C2C, the "
+                    "chunks are copied into a shared mapping of the output file")
+        crypt_file(src, dst, key, "ctr", iv, direct=True)
+        d = crypt_file(src, dst, key, "ctr", iv, direct=True)
+        r["direct_gbps"] = round(d["gbps"], 3) if d["direct"] else None
+        r["direct_how"] = ("opt-in direct path (AES_FILE_DIRECT): both files mapped, workers fault in each "
+                           "chunk's pages and the kernel reads and writes the mappings over NVLink-C2C")
         return r
 
 
-def scaling_study(torch, A):
+def scaling_study(torch, A, big, dst, sampler=None) -> dict:
     """The paper's throughput-vs-data-size and throughput-vs-parallel-instances
-    curves (its Figs. 4-9, on CPUs) restated for one GB300: AES-128 CTR GB/s
-    for buffers of 1 KiB .. 8 GiB, and for 1 .. all SMs' worth of CTAs on
-    1 GiB (one CTA per SM)."""
-    out = {"size_bytes": [], "size_gbps": [], "ctas": [], "ctas_gbps": []}
-    ks = A.aes_expand_key(synth.key_bytes(9, 128))
+    curves (its Figs. 4-9, on CPUs) restated for one GB300, compact enough for
+    every bench run: AES-128 CTR GB/s for buffers of 64 KiB .. the headline
+    buffer, AES-128 and AES-256 CTR at the single-buffer sweep's 64 MiB, 1 GiB
+    and 8 GiB, and AES-128 CTR on 1 GiB with 1 .. all SMs' worth of CTAs (one
+    CTA per SM).  Every point carries the clocks sampled while it ran."""
+    out = {"size_bytes": [], "size_gbps": [], "size_clocks_mhz": [],
+           "ctr_sweep": [], "ctas": [], "ctas_gbps": [], "ctas_clocks_mhz": []}
     iv = synth.iv_bytes(9)
-    big = synth.bytes_torch(9, synth.STREAM_DATA, 8 << 30, device="cuda")
-    dst = torch.empty_like(big)
-    for lg in range(10, 34, 2):  # 1 KiB .. 8 GiB
-        n = 1 << lg
+    n_big = big.numel()
+
+    def point(fn, nbytes, target_s=0.15, max_steps=2000):
+        one = time_device(torch, fn, 1, 2) / 1e3
+        steps = int(min(max_steps, max(5, target_s / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        ms = time_device(torch, fn, steps, 1)
+        t1 = time.perf_counter()
+        clk = sampler.summary(t0, t1) if sampler else {}
+        return round(nbytes * steps / (ms / 1e3) / 1e9, 2), clk
+
+    ks128 = A.aes_expand_key(synth.key_bytes(9, 128))
+    for n in (64 << 10, 1 << 20, 16 << 20, 64 << 20, 256 << 20, 1 << 30, 8 << 30):
+        if n > n_big:
+            break
         x, y = big[:n], dst[:n]
-        steps = int(min(2000, max(5, (4 << 30) // n)))
-        ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y), steps, 3)
+        g, clk = point(lambda: A.aes_ctr_xcrypt(ks128, iv, x, y), n)
         out["size_bytes"].append(n)
-        out["size_gbps"].append(round(n * steps / (ms / 1e3) / 1e9, 2))
-    n = 1 << 30
+        out["size_gbps"].append(g)
+        out["size_clocks_mhz"].append(clk.get("sm_mhz"))
+    for bits in (128, 256):
+        ks = A.aes_expand_key(synth.key_bytes(9, bits))
+        for n in (64 << 20, 1 << 30, 8 << 30):
+            if n > n_big:
+                continue
+            x, y = big[:n], dst[:n]
+            g, clk = point(lambda: A.aes_ctr_xcrypt(ks, iv, x, y), n, target_s=0.25)
+            out["ctr_sweep"].append({"bits": bits, "size_mib": n >> 20, "gbps": g, "clocks": clk})
+    n = min(1 << 30, n_big)
     x, y = big[:n], dst[:n]
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    for ctas in sorted({1, 2, 4, 8, 16, 32, 64, 96, 128, sms}):
+    for ctas in sorted({1, sms // 4, sms // 2, sms}):
         cfg = dict(variant=1, cta_threads=0, blocks_per_thread=0, grid_ctas=ctas)
-        steps = max(3, min(50, 2 * ctas))
-        ms = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, x, y, config=cfg), steps, 2)
+        g, clk = point(lambda: A.aes_ctr_xcrypt(ks128, iv, x, y, config=cfg), n, target_s=0.3, max_steps=50)
         out["ctas"].append(ctas)
-        out["ctas_gbps"].append(round(n * steps / (ms / 1e3) / 1e9, 2))
-    del big, dst
-    torch.cuda.empty_cache()
+        out["ctas_gbps"].append(g)
+        out["ctas_clocks_mhz"].append(clk.get("sm_mhz"))
     return out
 
 
@@ -845,7 +942,8 @@ def reference_arm(args):
         "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic: SplitMix64-seeded uniform random bytes",
         "config": {"workload": f"AES-{bits} {mode.upper()} of one {args.size_mib} MiB buffer per GPU, "
-                               "device-resident (single-buffer sweep, largest-buffer headline case)",
+                               "device-resident (single-buffer sweep 64 MiB / 1 GiB / 8 GiB; "
+                               + ("its largest buffer)" if args.size_mib == 8192 else "not its largest buffer)"),
                    "key_bits": bits, "mode": mode, "buffer_bytes": args.size_mib << 20},
         "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} bytes per step of the same workload, pthreads over {cores} threads"},

@@ -108,6 +108,17 @@ aes_status aes_ecb_decrypt(const aes_key_schedule *ks, const void *d_in, void *d
 aes_status aes_ctr_xcrypt(const aes_key_schedule *ks, const uint8_t iv[16], const void *d_in,
                           void *d_out, size_t nbytes, void *stream);
 
+/* The IV of a CTR range that starts `first_block` 16-byte blocks into a
+ * buffer (SP 800-38A §6.5, the counter blocks T_j): out_iv[0..11] = iv[0..11]
+ * and out_iv[12..15] = BE32((c0 + first_block) mod 2^32), c0 being
+ * iv[12..15] read big-endian; the counter wraps without carrying into the
+ * nonce, as in aes_ctr_xcrypt.  aes_ctr_xcrypt(out_iv, ...) on the bytes from
+ * 16 * first_block on therefore equals the same bytes of one call with `iv`
+ * on the whole buffer: the paper's chunk split (§IV.B) of a CTR buffer across
+ * calls, streams or GPUs.  iv, out_iv: host, 16 bytes each (may be the same
+ * array).  Synchronous, touches no GPU.  AES_ERR_ARG for a null pointer. */
+aes_status aes_ctr_iv_advance(const uint8_t iv[16], uint64_t first_block, uint8_t out_iv[16]);
+
 /* The same three calls with an explicit launch shape (cfg may be NULL, which
  * equals the plain call).  Every shape computes identical bytes. */
 aes_status aes_ecb_encrypt_ex(const aes_key_schedule *ks, const void *d_in, void *d_out,
@@ -130,6 +141,9 @@ aes_status aes_cbc_decrypt(const aes_key_schedule *ks, const uint8_t iv[16], con
                            void *d_out, size_t nbytes, void *stream);
 
 /* XTS-AES (IEEE 1619 / SP 800-38E) over data units of sector_bytes bytes,
+ * for the two key sizes those standards define: data_ks and tweak_ks both
+ * AES-128 or both AES-256 (any other pair, 192-bit keys included, returns
+ * AES_ERR_KEYSIZE),
  * without ciphertext stealing: sector_bytes a positive multiple of 512 and
  * nbytes a multiple of sector_bytes (AES_ERR_LENGTH).  Unit u (counted from
  * the start of d_in) uses the tweak value first_sector + u as a 128-bit
@@ -246,9 +260,11 @@ aes_status aes_batch_submit_ex(const aes_batch *b, void *d_workspace, size_t wor
  * aes_batch_submit, with the same rules and per-message status.
  *  - n_msgs above AES_BATCH_NOALLOC_MAX_MSGS returns AES_ERR_NOMEM and
  *    enqueues nothing.
- *  - The first call on a device looks up the array's device address there
- *    (cudaGetSymbolAddress, which may load the library's GPU code): make that
- *    first call before any stream capture on the device.
+ *  - The first call in a CUDA context looks up the array's device address
+ *    there (cudaGetSymbolAddress, which may load the library's GPU code) and
+ *    keeps it with that context's ID; a new context on the device (after
+ *    cudaDeviceReset, say) gets a fresh lookup.  Make the first call in a
+ *    context before any stream capture in it.
  *  - All calls on a device share the one array, and it keeps the last call's
  *    contents; the pipeline rewrites every part it reads (the first kernel
  *    resets the tile counter and rewrites the offsets) before use.  Two calls
@@ -265,9 +281,17 @@ aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
  *
  * Here the chunks are fixed-size pieces of the file handed to `threads`
  * worker threads, on one of two paths:
- *  - direct (when the current device reads and writes pageable host memory
- *    through the host's page tables, cudaDevAttrPageableMemoryAccess, as on
- *    Grace-Blackwell over NVLink-C2C): both files are mapped and the kernel
+ *  - staged (the default): each worker owns one pinned
+ *    host buffer and one CUDA stream and repeats: read its next chunk at the
+ *    chunk's file offset, run the cipher on the pinned buffer in place (the
+ *    kernel reads and writes host memory over the CPU-GPU link; no device
+ *    copy), wait for that stream, copy the chunk to the same offset of dst
+ *    (through a shared mapping of dst, or pwrite when dst cannot be mapped).
+ *    The GPU only ever touches the library's own pinned buffers.
+ *  - direct (opt-in with AES_FILE_DIRECT, taken when the current device reads
+ *    and writes pageable host memory through the host's page tables,
+ *    cudaDevAttrPageableMemoryAccess, as on Grace-Blackwell over NVLink-C2C;
+ *    otherwise the staged path runs): both files are mapped and the kernel
  *    reads the source chunk and writes the destination chunk in place in
  *    the mappings, no host copy.  Each worker first faults in its chunk's
  *    pages of both mappings, so the device never meets a missing page:
@@ -276,17 +300,13 @@ aes_status aes_batch_submit_noalloc(const aes_batch *b, void *stream);
  *    MADV_POPULATE_WRITE (one access per page on kernels without
  *    MADV_POPULATE_*).  It then launches the cipher on its own stream and
  *    takes the next chunk; each worker waits for its stream at the end.
- *  - staged (otherwise, or with AES_FILE_STAGED): each worker owns one pinned
- *    host buffer and one CUDA stream and repeats: read its next chunk at the
- *    chunk's file offset, run the cipher on the pinned buffer in place (the
- *    kernel reads and writes host memory over the CPU-GPU link; no device
- *    copy), wait for that stream, copy the chunk to the same offset of dst
- *    (through a shared mapping of dst, or pwrite when dst cannot be mapped).
- * Reads, writes and GPU work of different chunks overlap.  Another process
- * truncating src or dst during the call makes a mapped access fail (SIGBUS
- * on the host; on the direct path a device access to a page gone from the
- * mapping faults the CUDA context), as with any mapped file: the files must
- * keep their length while the call runs.  CTR chunks use the IV whose 32-bit
+ *    Hazard: if another process truncates src or dst while a chunk is in
+ *    flight, the kernel touches a page that no longer exists, which faults
+ *    the CUDA context (a host access would get SIGBUS).  Use this path only
+ *    for files that nothing else changes during the call.
+ * Reads, writes and GPU work of different chunks overlap.  On the staged
+ * path a truncation by another process during the call reaches only host
+ * code (SIGBUS on the shared mapping of dst), as with any mapped file.  CTR chunks use the IV whose 32-bit
  * counter is advanced by the chunk's first block (mod 2^32), so the output is
  * byte-identical to one call on the whole file; ECB needs a file length that
  * is a multiple of 16 (no padding here).
@@ -310,12 +330,14 @@ typedef enum aes_file_mode {
     AES_FILE_ECB_DECRYPT = 2
 } aes_file_mode;
 
-#define AES_FILE_STAGED 1u  /* take the staged path even where the direct one is possible */
+#define AES_FILE_STAGED 1u  /* the staged path (the default; the flag only makes it explicit) */
+#define AES_FILE_DIRECT 2u  /* opt in to the direct path where the device allows it (else staged);
+                               the caller promises that neither file changes length during the call */
 
 typedef struct aes_file_config {
     uint64_t chunk_bytes;  /* bytes per chunk: a multiple of 16; 0 = 64 MiB direct, 4 MiB staged */
     int32_t threads;       /* worker threads, 1..64; 0 = min(16, hardware threads) */
-    uint32_t flags;        /* 0 or AES_FILE_STAGED; other bits: AES_ERR_ARG */
+    uint32_t flags;        /* 0, AES_FILE_STAGED or AES_FILE_DIRECT; both or other bits: AES_ERR_ARG */
 } aes_file_config;
 
 typedef struct aes_file_stats {

@@ -478,3 +478,73 @@ int ref_ctr_xcrypt_mt(const uint8_t *key, int key_bits, const uint8_t iv[16], ui
                       const uint8_t *in, uint8_t *out, uint64_t n, int nthreads) {
     return run_chunks(2, key, key_bits, iv, first_block, in, out, n, nthreads);
 }
+
+/* ---- A list of messages over threads (the batched workloads) ----------- */
+
+typedef struct {
+    int op;
+    uint64_t n_msgs;
+    const uint8_t *in;
+    const uint64_t *in_off, *in_len, *out_off;
+    uint8_t *out;
+    const uint8_t *keys, *ivs;
+    const uint32_t *key_bits;
+    uint64_t *out_len;
+    int32_t *status;
+    uint64_t next; /* next unclaimed message, under mu */
+    pthread_mutex_t mu;
+} batch_t;
+
+static void batch_one(batch_t *b, uint64_t m) {
+    const uint8_t *key = b->keys + 32 * m;
+    const int bits = (int)b->key_bits[m];
+    const uint8_t *src = b->in + b->in_off[m];
+    uint8_t *dst = b->out + b->out_off[m];
+    const uint64_t n = b->in_len[m];
+    uint64_t olen = 0;
+    int rc;
+    if (b->op == 0) {
+        rc = ref_ctr_xcrypt(key, bits, b->ivs + 16 * m, 0, src, dst, n);
+        olen = n;
+    } else if (b->op == 1) {
+        rc = ref_ecb_pkcs7_encrypt(key, bits, src, n, dst, &olen);
+    } else {
+        rc = ref_ecb_pkcs7_decrypt(key, bits, src, n, dst, &olen);
+    }
+    b->status[m] = rc;
+    b->out_len[m] = rc == REF_OK ? olen : 0;
+}
+
+static void *batch_main(void *arg) {
+    batch_t *b = (batch_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&b->mu);
+        const uint64_t m = b->next;
+        if (m < b->n_msgs) b->next = m + 1;
+        pthread_mutex_unlock(&b->mu);
+        if (m >= b->n_msgs) return NULL;
+        batch_one(b, m);
+    }
+}
+
+int ref_batch_mt(int op, uint64_t n_msgs, const uint8_t *in, const uint64_t *in_off,
+                 const uint64_t *in_len, uint8_t *out, const uint64_t *out_off, const uint8_t *keys,
+                 const uint32_t *key_bits, const uint8_t *ivs, uint64_t *out_len, int32_t *status,
+                 int nthreads) {
+    if (op < 0 || op > 2) return REF_ERR_LENGTH;
+    if (nthreads < 1) nthreads = 1;
+    ensure_sbox(); /* build the shared table before any thread reads it */
+    batch_t b = {op, n_msgs, in, in_off, in_len, out_off, out, keys, ivs, key_bits, out_len, status, 0,
+                 PTHREAD_MUTEX_INITIALIZER};
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!th) return REF_ERR_THREAD;
+    int started = 0, rc = REF_OK;
+    for (; started < nthreads; ++started)
+        if (pthread_create(&th[started], NULL, batch_main, &b) != 0) { rc = REF_ERR_THREAD; break; }
+    if (started == 0) batch_main(&b); /* no thread could start: run the list here */
+    for (int t = 0; t < started; ++t)
+        if (pthread_join(th[t], NULL) != 0) rc = REF_ERR_THREAD;
+    free(th);
+    pthread_mutex_destroy(&b.mu);
+    return rc;
+}

@@ -108,6 +108,23 @@ int ref_ecb_decrypt_mt(const uint8_t *key, int key_bits, const uint8_t *in, uint
 int ref_ctr_xcrypt_mt(const uint8_t *key, int key_bits, const uint8_t iv[16], uint64_t first_block,
                       const uint8_t *in, uint8_t *out, uint64_t n, int nthreads);
 
+/* A list of independent messages, each with its own key (and IV): message m
+ * is in[in_off[m] .. in_off[m] + in_len[m]), its key the first key_bits[m]/8
+ * bytes of keys + 32m, its IV (CTR) ivs + 16m.  op 0: CTR
+ * (ref_ctr_xcrypt, output in_len[m] bytes); op 1: PKCS#7 then ECB
+ * (ref_ecb_pkcs7_encrypt); op 2: ECB decryption then the PKCS#7 check
+ * (ref_ecb_pkcs7_decrypt, the whole decrypted length written, out_len[m] the
+ * unpadded one).  Output m goes to out + out_off[m]; status[m] gets the
+ * message's REF_* code and out_len[m] its output length (0 on failure).  The
+ * messages are shared out to nthreads threads, each taking the next unclaimed
+ * message in turn (the paper's chunk-per-thread scheme with chunks =
+ * messages); every message runs the single-threaded routine on its own.
+ * Returns REF_OK, or REF_ERR_THREAD / REF_ERR_LENGTH (unknown op). */
+int ref_batch_mt(int op, uint64_t n_msgs, const uint8_t *in, const uint64_t *in_off,
+                 const uint64_t *in_len, uint8_t *out, const uint64_t *out_off, const uint8_t *keys,
+                 const uint32_t *key_bits, const uint8_t *ivs, uint64_t *out_len, int32_t *status,
+                 int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,9 @@ def _declare(lib):
         getattr(lib, name).argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, u8p, u8p,
                                        ctypes.c_uint64]
         getattr(lib, name).restype = ctypes.c_int
+    lib.ref_batch_mt.argtypes = [ctypes.c_int, ctypes.c_uint64, u8p, u8p, u8p, u8p, u8p, u8p, u8p, u8p, u8p,
+                                 u8p, ctypes.c_int]
+    lib.ref_batch_mt.restype = ctypes.c_int
     lib.ref_pkcs7_padded_len.argtypes = [ctypes.c_uint64]
     lib.ref_pkcs7_padded_len.restype = ctypes.c_uint64
     for name in ("ref_ecb_pkcs7_encrypt", "ref_ecb_pkcs7_decrypt"):
@@ -221,6 +224,40 @@ class Oracle:
                                             _ptr(out), ix.size)
         _check(rc, "ctr_xcrypt_blocks")
         return out
+
+    def batch(self, op: int, data, in_off, in_len, out_size: int, out_off, keys, key_bits, ivs=None,
+              nthreads: int = 1, out=None):
+        """A list of messages (op 0 CTR, 1 PKCS#7 + ECB encrypt, 2 ECB decrypt
+        + PKCS#7 check), each with its own key and IV, one oracle call per
+        message.  Returns (out arena of out_size bytes, out_len, status);
+        ``out`` (optional) is an arena to write into, whose bytes outside the
+        messages' outputs are left as they are."""
+        d = _u8(data)
+        io = np.ascontiguousarray(np.asarray(in_off, np.uint64).reshape(-1))
+        il = np.ascontiguousarray(np.asarray(in_len, np.uint64).reshape(-1))
+        oo = np.ascontiguousarray(np.asarray(out_off, np.uint64).reshape(-1))
+        n = io.size
+        assert il.size == n and oo.size == n
+        k = np.ascontiguousarray(np.asarray(keys, np.uint8).reshape(n, 32))
+        kb = np.ascontiguousarray(np.asarray(key_bits, np.uint32).reshape(-1))
+        assert kb.size == n
+        if op == 0:
+            v = np.ascontiguousarray(np.asarray(ivs, np.uint8).reshape(n, 16))
+        else:
+            v = np.zeros((max(n, 1), 16), np.uint8)
+        # every message must lie inside the arenas it reads and writes
+        if n:
+            assert int((io + il).max()) <= d.size
+            span = il if op != 1 else (il - il % np.uint64(16) + np.uint64(16))
+            assert int((oo + span).max()) <= out_size
+        o = np.zeros(out_size, np.uint8) if out is None else out
+        assert o.dtype == np.uint8 and o.flags.c_contiguous and o.size == out_size
+        out_len = np.zeros(max(n, 1), np.uint64)
+        status = np.zeros(max(n, 1), np.int32)
+        rc = self.lib.ref_batch_mt(op, n, _ptr(d), _ptr(io), _ptr(il), _ptr(o), _ptr(oo), _ptr(k), _ptr(kb),
+                                   _ptr(v), _ptr(out_len), _ptr(status), nthreads)
+        _check(rc, "batch")
+        return o, out_len[:n], status[:n]
 
     def pkcs7_padded_len(self, n: int) -> int:
         return int(self.lib.ref_pkcs7_padded_len(n))

@@ -69,6 +69,8 @@ def lib():
             getattr(L, name + "_ex").argtypes = [ksp, vp, vp, sz, vp, cfgp]
         L.aes_ctr_xcrypt.argtypes = [ksp, vp, vp, vp, sz, vp]
         L.aes_ctr_xcrypt_ex.argtypes = [ksp, vp, vp, vp, sz, vp, cfgp]
+        L.aes_ctr_iv_advance.argtypes = [vp, ctypes.c_uint64, vp]
+        L.aes_ctr_iv_advance.restype = ctypes.c_int
         L.aes_cbc_decrypt.argtypes = [ksp, vp, vp, vp, sz, vp]
         for name in ("aes_xts_encrypt", "aes_xts_decrypt"):
             getattr(L, name).argtypes = [ksp, ksp, ctypes.c_uint64, sz, vp, vp, sz, vp]
@@ -168,6 +170,21 @@ def aes_ctr_xcrypt(ks: KeySchedule, iv, inp, out=None, stream=None, config=None)
                                    out.data_ptr(), inp.numel(), _stream_handle(stream, inp),
                                    _cfg(config)), "aes_ctr_xcrypt")
     return out
+
+
+def aes_ctr_iv_advance(iv, first_block: int) -> bytes:
+    """The IV of a CTR range starting ``first_block`` blocks into a buffer
+    (the library's counter advance, modulo 2^32, nonce unchanged)."""
+    v = _host_bytes(iv)
+    if v.size != 16:
+        raise ValueError("iv must be 16 bytes")
+    if first_block < 0:
+        raise ValueError("first_block must be >= 0")
+    vb = (ctypes.c_uint8 * 16).from_buffer_copy(v.tobytes())
+    out = (ctypes.c_uint8 * 16)()
+    _check(lib().aes_ctr_iv_advance(ctypes.cast(vb, ctypes.c_void_p), first_block,
+                                    ctypes.cast(out, ctypes.c_void_p)), "aes_ctr_iv_advance")
+    return bytes(out)
 
 
 def aes_cbc_decrypt(ks: KeySchedule, iv, inp, out=None, stream=None):

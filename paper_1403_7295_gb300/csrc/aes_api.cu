@@ -270,6 +270,9 @@ aes_status run_xts(bool decrypt, const aes_key_schedule* data_ks, const aes_key_
   if (s != AES_OK) return s;
   s = check_schedule(tweak_ks);
   if (s != AES_OK) return s;
+  // IEEE 1619 / SP 800-38E define XTS-AES-128 and XTS-AES-256 only: two
+  // 128-bit or two 256-bit halves of the XTS key.
+  if (data_ks->key_bits != tweak_ks->key_bits || data_ks->key_bits == 192) return AES_ERR_KEYSIZE;
   if (sector_bytes == 0 || sector_bytes % 512 != 0 || sector_bytes / 16 > 0xFFFFFFFFull ||
       nbytes % sector_bytes != 0)
     return AES_ERR_LENGTH;
@@ -402,6 +405,22 @@ aes_status aes_expand_key(const uint8_t* key, int key_bits, aes_key_schedule* ks
       const uint32_t v = w[4 * (nr - r) + c];
       ks->rk_dec[4 * r + c] = (r == 0 || r == nr) ? v : inv_mix_word(v);
     }
+  return AES_OK;
+}
+
+// SP 800-38A §6.5: counter block T_{first_block} of a buffer whose block 0
+// uses `iv`; only the 32-bit big-endian counter in bytes 12..15 moves.
+aes_status aes_ctr_iv_advance(const uint8_t iv[16], uint64_t first_block, uint8_t out_iv[16]) {
+  if (iv == nullptr || out_iv == nullptr) return AES_ERR_ARG;
+  uint8_t v[16];
+  std::memcpy(v, iv, 16);  // iv and out_iv may be the same array
+  const uint32_t c0 = ((uint32_t)v[12] << 24) | ((uint32_t)v[13] << 16) | ((uint32_t)v[14] << 8) | v[15];
+  const uint32_t c = c0 + static_cast<uint32_t>(first_block);  // modulo 2^32, no carry into the nonce
+  v[12] = static_cast<uint8_t>(c >> 24);
+  v[13] = static_cast<uint8_t>(c >> 16);
+  v[14] = static_cast<uint8_t>(c >> 8);
+  v[15] = static_cast<uint8_t>(c);
+  std::memcpy(out_iv, v, 16);
   return AES_OK;
 }
 

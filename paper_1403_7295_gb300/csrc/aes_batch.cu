@@ -833,12 +833,6 @@ __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total, u
 // one ballot (messages starting at or before `base`) and one OR-reduction (a
 // bit for every message starting inside the step), so there is no search.
 
-// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
-// multiple of 16): no data is returned, nothing waits on it.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // One message of a group (block numbers relative to the group).
 struct GroupMsg {
   uint64_t src0, dst0;  // byte address of (virtual) group block 0 in the message's input / output
@@ -957,12 +951,6 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
         nb = static_cast<uint32_t>(b);
         len = a.in_len[m0 + lane];
       }
-    }
-    if (nb > 0) {
-      // Start moving the message's whole blocks into L2 while the keys are
-      // expanded (a hint: whole 16-byte blocks only, never past the message).
-      const uint32_t bytes = static_cast<uint32_t>(len & ~15ull);
-      if (bytes >= 16) prefetch_l2(a.in + a.in_off[m0 + lane], bytes);
     }
     const uint32_t valid = __ballot_sync(0xffffffffu, nb > 0);
     uint32_t nr = 0;  // the lane's message's rounds (0: no message)

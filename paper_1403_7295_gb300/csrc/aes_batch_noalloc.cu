@@ -2,6 +2,7 @@
 // the batch pipeline's workspace (per-message block offsets, chunk totals,
 // tile counter) lives in one file-scope device array instead of a caller
 // buffer.  The work itself is the ordinary aes_batch_submit path.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,28 +24,79 @@ constexpr size_t kScratchBytes = workspace_for(AES_BATCH_NOALLOC_MAX_MSGS);  // 
 // Held by every device that loads the library, for the life of the process.
 static __device__ __align__(256) unsigned char g_batch_scratch[kScratchBytes];
 
-// Device address of g_batch_scratch per device ordinal, looked up once with
-// that device current.  The host-side symbol is only a handle: its own
-// address is not usable on the device.
+// Device address of g_batch_scratch per device ordinal, looked up with that
+// device current and kept with the ID of the CUDA context it was looked up
+// in.  The host-side symbol is only a handle: its own address is not usable
+// on the device.  A new context on the device (after cudaDeviceReset, or a
+// driver-API context made current) has a new ID and gets a fresh lookup, so
+// a stale address from a destroyed context is never handed to a kernel.
 constexpr int kMaxDevices = 64;
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  void* ptr;
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxDevices] = {};
+
+// The two driver calls that name the current context, fetched through the
+// runtime (so the library needs no link against the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+struct DriverCalls {
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+  bool ok = false;
+};
+
+const DriverCalls& driver_calls() {
+  static const DriverCalls calls = [] {
+    DriverCalls c;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    // cuCtxGetId exists from CUDA 12.0 on.
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2) {
+      c.get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      c.get_id = reinterpret_cast<CtxGetIdFn>(f2);
+      c.ok = true;
+    }
+    return c;
+  }();
+  return calls;
+}
+
+// ID of the calling thread's current context, 0 if there is none yet.
+bool current_context_id(unsigned long long* id) {
+  const DriverCalls& d = driver_calls();
+  if (!d.ok) return false;
+  CUcontext ctx = nullptr;
+  if (d.get_current(&ctx) != CUDA_SUCCESS) return false;
+  *id = 0;
+  return ctx == nullptr || d.get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 aes_status scratch_for_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
   if (dev < 0 || dev >= kMaxDevices) return AES_ERR_ARG;
+  unsigned long long id = 0;
+  if (!current_context_id(&id)) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  ScratchEntry& entry = g_scratch[dev];
+  if (id == 0 || entry.ptr == nullptr || entry.ctx_id != id) {
     if (aesgpu::batch_workspace_bytes(AES_BATCH_NOALLOC_MAX_MSGS) > kScratchBytes)
       return AES_ERR_NOMEM;  // layout drifted from the sizing above
     void* p = nullptr;
+    // Binds (or creates) the device's primary context when none is current.
     e = cudaGetSymbolAddress(&p, g_batch_scratch);
     if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
-    g_scratch_ptr[dev] = p;
+    if (!current_context_id(&id) || id == 0) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
+    entry = ScratchEntry{id, p};
   }
-  *out = g_scratch_ptr[dev];
+  *out = entry.ptr;
   return AES_OK;
 }
 

@@ -2,14 +2,14 @@
 // paper's workload, §IV), as a pipeline of worker threads over chunks.  Host
 // code only; the cipher runs through the library's own single-buffer path.
 //
-// Direct path (the device reads and writes pageable host memory through the
-// host's page tables): both files are mapped, each worker faults in its
+// Direct path (opt-in, AES_FILE_DIRECT; the device reads and writes pageable
+// host memory through the host's page tables): both files are mapped, each worker faults in its
 // chunk's pages and launches the cipher on the mappings themselves, so no
 // byte is copied on the host.  On the GB300 host the kernel moves mapped
 // file pages over NVLink-C2C as fast as pinned buffers (about 170 GB/s each
 // way).
 //
-// Staged path (otherwise): input chunks are read with pread at their offsets
+// Staged path (the default): input chunks are read with pread at their offsets
 // into pinned buffers (parallel reads of one file scale with the threads),
 // the kernel runs on the pinned buffer in place, and output chunks are
 // copied into a shared mapping of dst: writes to one file through
@@ -127,17 +127,9 @@ struct FileJob {
   }
 };
 
-// The IV whose 32-bit big-endian counter (bytes 12..15) is advanced by
-// `blocks` modulo 2^32; the nonce bytes are unchanged.
-void iv_at(const uint8_t iv[16], uint64_t blocks, uint8_t out[16]) {
-  std::memcpy(out, iv, 16);
-  uint32_t c = (uint32_t(iv[12]) << 24) | (uint32_t(iv[13]) << 16) | (uint32_t(iv[14]) << 8) | iv[15];
-  c += static_cast<uint32_t>(blocks);
-  out[12] = uint8_t(c >> 24);
-  out[13] = uint8_t(c >> 16);
-  out[14] = uint8_t(c >> 8);
-  out[15] = uint8_t(c);
-}
+// The IV of the chunk starting `blocks` blocks into the file: the library's
+// aes_ctr_iv_advance (counter in bytes 12..15 advanced modulo 2^32).
+void iv_at(const uint8_t iv[16], uint64_t blocks, uint8_t out[16]) { aes_ctr_iv_advance(iv, blocks, out); }
 
 bool read_full(int fd, uint8_t* p, uint64_t n, uint64_t off, int* err) {
   while (n > 0) {
@@ -310,7 +302,8 @@ extern "C" aes_status aes_file_crypt(const char* src_path, const char* dst_path,
   uint64_t chunk = cfg ? cfg->chunk_bytes : 0;  // 0: the path's default, set below
   int threads = cfg && cfg->threads ? cfg->threads : 0;
   const uint32_t flags = cfg ? cfg->flags : 0u;
-  if (flags & ~AES_FILE_STAGED) return AES_ERR_ARG;
+  if ((flags & ~(AES_FILE_STAGED | AES_FILE_DIRECT)) || flags == (AES_FILE_STAGED | AES_FILE_DIRECT))
+    return AES_ERR_ARG;
   if (chunk % 16 != 0 || threads < 0 || threads > kMaxThreads) return AES_ERR_ARG;
   if (threads == 0) {
     const unsigned hw = std::thread::hardware_concurrency();
@@ -355,11 +348,13 @@ extern "C" aes_status aes_file_crypt(const char* src_path, const char* dst_path,
   aes_status result = AES_OK;
   // an empty file needs no GPU: dst is created empty and nothing else runs
   cudaError_t ce = job.size > 0 ? cudaGetDevice(&job.device) : cudaSuccess;
-  // the direct path: dst mapped, src mapped (or the same mapping in place),
-  // and a device that reaches pageable memory through the host's page tables
+  // the direct path, only when asked for: dst mapped, src mapped (or the
+  // same mapping in place), and a device that reaches pageable memory through
+  // the host's page tables.  It is opt-in because a file truncated by another
+  // process while a chunk is in flight would fault the device, not the host.
   bool direct = false;
   uint8_t* src_map = nullptr;  // a mapping of its own (not in place)
-  if (ce == cudaSuccess && job.size > 0 && job.map && !(flags & AES_FILE_STAGED) && host_pageable_access()) {
+  if (ce == cudaSuccess && job.size > 0 && job.map && (flags & AES_FILE_DIRECT) && host_pageable_access()) {
     if (same) {
       job.src_map = job.map;
       direct = true;

@@ -1,11 +1,13 @@
 """Encrypt or decrypt a file on the GPU: the paper's workload (a file in, the
 encrypted file out, §IV), through the library's native pipeline
 ``aes_file_crypt`` (include/aesgpu.h).  Worker threads take fixed-size
-chunks.  Where the device reaches pageable host memory through the host's
-page tables (Grace-Blackwell over NVLink-C2C), both files are mapped and the
-kernel reads and writes the mapped chunks directly (the direct path, no host
-copy); otherwise each worker reads its chunk into a pinned buffer, runs the
-cipher on it in place and copies it into the output (the staged path).  CTR
+chunks.  By default each worker reads its chunk into a pinned buffer, runs
+the cipher on it in place and copies it into the output (the staged path).
+With ``direct=True`` (``--direct``), where the device reaches pageable host
+memory through the host's page tables (Grace-Blackwell over NVLink-C2C),
+both files are mapped and the kernel reads and writes the mapped chunks
+directly (no host copy); the files must then keep their length during the
+call, since a page truncated away under a running kernel faults the GPU.  CTR
 chunks use the IV advanced by the chunk's first block, so the result is
 byte-identical to one call on the whole file.  ECB needs a file length that
 is a multiple of 16 (no padding here).
@@ -25,7 +27,8 @@ from . import aes as _aes
 MODES = {"ctr": 0, "ecb-enc": 1, "ecb-dec": 2}
 
 
-STAGED = 1  # AES_FILE_STAGED: take the staged path even where the direct one is possible
+STAGED = 1  # AES_FILE_STAGED: the staged path (the default)
+DIRECT = 2  # AES_FILE_DIRECT: opt in to the direct path where the device allows it
 
 
 class FileConfig(ctypes.Structure):
@@ -52,11 +55,12 @@ def _declare():
 
 
 def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes: int = 0,
-               threads: int = 0, staged: bool = False) -> dict:
+               threads: int = 0, direct: bool = False) -> dict:
     """Process `src` into `dst` (the same path encrypts in place); returns
     bytes, chunks, seconds (of which setup), worker threads, whether the
     direct path ran, and GB/s file to file.  chunk_bytes 0 takes the path's
-    default (64 MiB direct, 4 MiB staged); `staged` forces the staged path.
+    default (64 MiB direct, 4 MiB staged); `direct` opts in to the direct path
+    (taken where the device reaches pageable memory; else staged).
     Raises ValueError for a bad mode, IV or ragged ECB length, and OSError /
     AesError when the native call fails."""
     if mode not in MODES:
@@ -69,7 +73,7 @@ def crypt_file(src: str, dst: str, key, mode: str = "ctr", iv=None, chunk_bytes:
         raise ValueError("ECB needs a file length that is a multiple of 16")
     ks = _aes.aes_expand_key(key)
     ivb = ctypes.create_string_buffer(bytes(iv), 16) if mode == "ctr" else None
-    cfg = FileConfig(chunk_bytes, threads, STAGED if staged else 0)
+    cfg = FileConfig(chunk_bytes, threads, DIRECT if direct else 0)
     st = FileStats()
     rc = _declare().aes_file_crypt(os.fsencode(src), os.fsencode(dst), MODES[mode], ctypes.byref(ks),
                                    ivb, ctypes.byref(cfg), ctypes.byref(st))
@@ -95,11 +99,12 @@ def main():
     p.add_argument("--iv", default=None, help="hex, 16 bytes (CTR)")
     p.add_argument("--chunk-mib", type=int, default=0, help="0: the path's default")
     p.add_argument("--threads", type=int, default=0)
-    p.add_argument("--staged", action="store_true", help="pinned buffers even where the files could be mapped")
+    p.add_argument("--direct", action="store_true",
+                   help="run the kernel on the mapped files (the files must not change length meanwhile)")
     a = p.parse_args()
     iv = bytes.fromhex(a.iv) if a.iv else None
     r = crypt_file(a.src, a.dst, np.frombuffer(bytes.fromhex(a.key), np.uint8), a.mode, iv,
-                   a.chunk_mib << 20, a.threads, a.staged)
+                   a.chunk_mib << 20, a.threads, a.direct)
     print(r)
 
 

@@ -189,6 +189,8 @@ class Server:
             "p99_ms": float(np.percentile(lat[ok], 99) * 1e3) if ok.any() else None,
             "max_ms": float(lat[ok].max() * 1e3) if ok.any() else None,
             "admission_wait_p99_ms": float(np.percentile(wait[ok], 99) * 1e3) if ok.any() else None,
+            "admission_wait_mean_ms": float(wait[ok].mean() * 1e3) if ok.any() else None,
+            "admission_wait_max_ms": float(wait[ok].max() * 1e3) if ok.any() else None,
             "batches": st["batches"], "mean_batch_msgs": st["mean_batch_msgs"],
             "batches_launched_while_previous_in_flight": st["batches_overlapped"],
             "max_budget_charged": st["max_charged"], "budget": self.budget,

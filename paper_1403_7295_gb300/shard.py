@@ -8,7 +8,8 @@ offsets (the paper's concatenation step disappears).  The remainder blocks
 and any partial CTR tail go to the last rank, as the paper's last chunk
 takes the remainder.  For CTR a range starting at block b uses the IV whose
 32-bit big-endian counter is advanced by b (modulo 2^32, no carry into the
-nonce), so every rank produces exactly the bytes of the single-pass call.
+nonce, computed by the library's ``aes_ctr_iv_advance``), so every rank
+produces exactly the bytes of the single-pass call.
 """
 from __future__ import annotations
 
@@ -38,9 +39,9 @@ def shard_ranges(nbytes: int, world: int) -> list[Shard]:
 
 
 def ctr_iv_at(iv, first_block: int) -> bytes:
-    """IV of a CTR range that starts at block `first_block` of the buffer."""
-    iv = bytes(iv)
-    if len(iv) != 16:
-        raise ValueError("iv must be 16 bytes")
-    c0 = int.from_bytes(iv[12:16], "big")
-    return iv[:12] + ((c0 + first_block) % (1 << 32)).to_bytes(4, "big")
+    """IV of a CTR range that starts at block `first_block` of the buffer:
+    the library's ``aes_ctr_iv_advance`` (the counter arithmetic stays behind
+    the C ABI; this only marshals)."""
+    from .aes import aes_ctr_iv_advance
+
+    return aes_ctr_iv_advance(iv, first_block)

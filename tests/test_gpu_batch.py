@@ -7,9 +7,12 @@ block-sized and ragged messages; batches large enough for the chunked scan
 (> 4096 messages) and for many key windows per tile (thousands of one-block
 messages per tile); per-message failures (bad key size, misaligned offset,
 bad ECB length, bad padding) that leave the rest of the batch intact;
-CUDA-graph replay; and the full-size batched workloads (16,384 log-uniform
-messages, 64 B .. 4 MiB; 1,000,000 packet-sized messages) on sampled
-messages.
+CUDA-graph replay; and the full-size batched workloads: all 1,000,000
+packet-sized messages compared whole, and of the 16,384 log-uniform messages
+(64 B .. 4 MiB) every message up to 1 MiB compared whole and the larger ones
+on sampled blocks, for CTR and for ECB+PKCS#7 encryption and decryption.
+The whole-message compares run the oracle's message list over all host
+threads.
 """
 import ctypes
 
@@ -408,39 +411,98 @@ def sampled_check_large(B, oracle, b, key_bits, keys, ivs, ms, max_full=1 << 20)
             assert np.array_equal(got.reshape(-1), want), m
 
 
+def oracle_list_check(B, oracle, b, key_bits, keys, ivs, ms):
+    """Messages `ms` of batch `b` against the oracle's message list (one
+    oracle call per message, all host threads): output bytes, status and
+    output length.  The oracle writes its outputs over a copy of the GPU's
+    output arena, so the two arenas are equal exactly when every checked
+    message is."""
+    ms = np.asarray(ms, np.int64)
+    data = b.data.cpu().numpy()
+    got = b.out.cpu().numpy()
+    status = b.status.cpu().numpy()[ms]
+    out_len = b.out_len.cpu().numpy()[ms]
+    in_off = b.in_off.cpu().numpy().astype(np.uint64)[ms]
+    ivs_m = np.asarray(ivs)[ms] if ivs is not None else None
+    want, want_len, want_st = oracle.batch(b.op, data, in_off, b.lengths_np[ms], got.size, b.out_off_np[ms],
+                                           np.asarray(keys)[ms], np.asarray(key_bits)[ms], ivs_m,
+                                           nthreads=host_threads(), out=got.copy())
+    # the library's status codes: 0 ok, 6 AES_ERR_PADDING (the oracle's -3)
+    assert np.array_equal(status, np.where(want_st == 0, 0, np.where(want_st == -3, 6, -100)))
+    assert np.array_equal(out_len.astype(np.uint64), want_len)
+    mism = np.flatnonzero(got != want)
+    assert mism.size == 0, f"{mism.size} output bytes differ, first at {mism[:4]}"
+
+
+def sampled_check_large_ecb(B, oracle, b, key_bits, keys, ms, decrypt):
+    """ECB messages compared on 256 sampled whole blocks each (block j of the
+    output is the cipher, or inverse cipher, of block j of the input; the
+    padded last block is covered by the whole-message compares)."""
+    import torch
+
+    for m in ms:
+        ln = int(b.lengths_np[m])
+        bits = int(key_bits[m])
+        key = keys[m][: bits // 8]
+        io = int(b.in_off[m].item())
+        oo = int(b.out_off_np[m])
+        nb = ln // 16
+        idx = np.unique((synth.uniform01(m, synth.STREAM_MISC, 256) * nb).astype(np.int64))
+        t = torch.from_numpy(idx).cuda()
+        blocks = b.data[io: io + 16 * nb].view(-1, 16)[t].cpu().numpy().reshape(-1)
+        got = b.out[oo: oo + 16 * nb].view(-1, 16)[t].cpu().numpy().reshape(-1)
+        want = oracle.ecb_decrypt(key, bits, blocks) if decrypt else oracle.ecb_encrypt(key, bits, blocks)
+        assert np.array_equal(got, want), m
+
+
 def test_full_size_batched_varlen_16384(torch, B, oracle):
-    """16,384 messages, log-uniform 64 B .. 4 MiB, mixed key sizes (≈6 GB):
-    CTR sampled against the oracle; ECB+PKCS#7 encrypt then decrypt on the
-    device gives back every message."""
+    """16,384 messages, log-uniform 64 B .. 4 MiB, mixed key sizes (about
+    6 GB), at the autotuned shape in a CUDA graph: every message up to 1 MiB
+    compared whole with the oracle (about 1.5 GB), the larger ones on 256
+    sampled blocks each; then the same for ECB+PKCS#7 encryption, and for
+    decryption of that ciphertext (padding checked, lengths restored)."""
     wl = W.batched_varlen(3, 16384)
     lengths, kb, keys, ivs = wl["lengths"], wl["key_bits"], wl["keys"], wl["ivs"]
+    small = np.flatnonzero(lengths <= (1 << 20))
+    large = np.flatnonzero(lengths > (1 << 20))
+    assert small.size > 14000 and large.size > 1000
     b = build(B, torch, 0, lengths, kb, keys, ivs, seed=19)
     b.capture(B.autotune(b))
     b.replay()
     torch.cuda.synchronize()
     assert int((b.status != 0).sum()) == 0
-    pick = np.unique((synth.uniform01(19, synth.STREAM_MISC, 48) * b.n).astype(np.int64))
-    biggest = int(np.argmax(lengths))
-    sampled_check_large(B, oracle, b, kb, keys, ivs, list(pick) + [biggest, 0, b.n - 1])
+    oracle_list_check(B, oracle, b, kb, keys, ivs, small)
+    sampled_check_large(B, oracle, b, kb, keys, ivs, large)
     del b
     torch.cuda.empty_cache()
-    enc = build(B, torch, 1, lengths, kb, keys, None, seed=20).submit()
+    enc = build(B, torch, 1, lengths, kb, keys, None, seed=20)
+    enc.capture(B.autotune(enc))
+    enc.replay()
     torch.cuda.synchronize()
+    assert int((enc.status != 0).sum()) == 0
+    oracle_list_check(B, oracle, enc, kb, keys, None, small)
+    sampled_check_large_ecb(B, oracle, enc, kb, keys, large, decrypt=False)
     ct_len = enc.out_len.cpu().numpy().astype(np.uint64)
-    oracle_check(B, oracle, enc, kb, keys, None, idx=[m for m in range(0, 16384, 512) if lengths[m] < (1 << 18)])
-    dec = B.Batch(2, enc.out, enc.out_off_np, ct_len, keys=keys, key_bits=kb).submit()
+    assert np.array_equal(ct_len, lengths - lengths % np.uint64(16) + np.uint64(16))
+    dec = B.Batch(2, enc.out, enc.out_off_np, ct_len, keys=keys, key_bits=kb)
+    dec.capture(B.autotune(dec))
+    dec.replay()
     torch.cuda.synchronize()
     assert int((dec.status != 0).sum()) == 0
     assert np.array_equal(dec.out_len.cpu().numpy(), lengths.astype(np.int64))
-    # plaintext back, compared on the device message by message (offsets differ only by padding)
+    oracle_list_check(B, oracle, dec, kb, keys, None, small)
+    sampled_check_large_ecb(B, oracle, dec, kb, keys, large, decrypt=True)
+    # and the plaintext back, message by message on the device (offsets differ only by padding)
     src_off = enc.in_off.cpu().numpy()
-    for m in range(0, 16384, 97):
+    for m in large:
         ln, o, i = int(lengths[m]), int(dec.out_off_np[m]), int(src_off[m])
         assert torch.equal(dec.out[o: o + ln], enc.data[i: i + ln]), m
 
 
 def test_full_size_small_messages_1M(torch, B, oracle):
-    """1,000,000 messages of 16..1500 bytes, AES-128 CTR, keys expanded on the device."""
+    """1,000,000 messages of 16..1500 bytes, AES-128 CTR, keys expanded on the
+    device, at the autotuned shape in a CUDA graph: every message compared
+    whole with the oracle."""
     wl = W.small_messages(4, 1_000_000)
     lengths, kb, keys, ivs = wl["lengths"], wl["key_bits"], wl["keys"], wl["ivs"]
     b = build(B, torch, 0, lengths, kb, keys, ivs, seed=21)
@@ -448,8 +510,7 @@ def test_full_size_small_messages_1M(torch, B, oracle):
     b.replay()
     torch.cuda.synchronize()
     assert int((b.status != 0).sum()) == 0
-    pick = np.unique((synth.uniform01(21, synth.STREAM_MISC, 2000) * b.n).astype(np.int64))
-    oracle_check(B, oracle, b, kb, keys, ivs, idx=list(pick) + [0, b.n - 1])
+    oracle_list_check(B, oracle, b, kb, keys, ivs, np.arange(b.n))
 
 
 def test_batch_randomized_shapes(torch, B, oracle):

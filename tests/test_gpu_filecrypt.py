@@ -1,9 +1,9 @@
 """File encryption pipeline (aes_file_crypt): file in, encrypted file out,
 byte-identical to one library call on the whole buffer and to the oracle,
 across many chunks with a ragged end, for CTR and ECB, any number of worker
-threads, in place on the same file, and back again; on both paths (files
-mapped and processed by the kernel directly, or staged through pinned
-buffers)."""
+threads, in place on the same file, and back again; on both paths (staged
+through pinned buffers, the default, or, opted in, files mapped and
+processed by the kernel directly)."""
 import os
 import tempfile
 
@@ -14,7 +14,7 @@ import synth
 from tests.gpu_util import pageable_memory_access, require_cuda
 
 pytestmark = pytest.mark.gpu
-PATHS = pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+PATHS = pytest.mark.parametrize("direct", [True, False], ids=["direct", "staged"])
 
 
 @pytest.fixture(scope="module")
@@ -23,7 +23,7 @@ def torch():
 
 
 @PATHS
-def test_ctr_file_round_trip(torch, oracle, staged):
+def test_ctr_file_round_trip(torch, oracle, direct):
     from paper_1403_7295_gb300 import aes as A
     from paper_1403_7295_gb300.filecrypt import crypt_file
 
@@ -34,20 +34,20 @@ def test_ctr_file_round_trip(torch, oracle, staged):
     with tempfile.TemporaryDirectory() as d:
         src, enc, dec = (os.path.join(d, f) for f in ("p", "c", "q"))
         data.tofile(src)
-        r = crypt_file(src, enc, key, "ctr", iv, chunk_bytes=4 << 20, threads=3, staged=staged)
+        r = crypt_file(src, enc, key, "ctr", iv, chunk_bytes=4 << 20, threads=3, direct=direct)
         assert r["bytes"] == n and r["chunks"] == 7 and r["threads"] == 3
-        assert r["direct"] == (not staged and bool(pageable_memory_access()))
+        assert r["direct"] == (direct and bool(pageable_memory_access()))
         got = np.fromfile(enc, np.uint8)
         whole = A.aes_ctr_xcrypt(A.aes_expand_key(key), iv, torch.from_numpy(data).cuda()).cpu().numpy()
         assert np.array_equal(got, whole)
         assert np.array_equal(got[: 1 << 20], oracle.ctr_xcrypt(key, 192, np.frombuffer(iv, np.uint8), data[: 1 << 20]))
-        crypt_file(enc, dec, key, "ctr", iv, chunk_bytes=8 << 20, threads=2, staged=staged)
+        crypt_file(enc, dec, key, "ctr", iv, chunk_bytes=8 << 20, threads=2, direct=direct)
         assert np.array_equal(np.fromfile(dec, np.uint8), data)
 
 
 @PATHS
 @pytest.mark.parametrize("n", [1, 15, 16, 17, 1000, 4096 + 3, (1 << 16) + 48])
-def test_ctr_small_files_tiny_chunks(torch, oracle, n, staged):
+def test_ctr_small_files_tiny_chunks(torch, oracle, n, direct):
     """Files shorter than a block and chunks of one block: every chunk is its
     own launch with its own advanced IV."""
     from paper_1403_7295_gb300.filecrypt import crypt_file
@@ -60,12 +60,12 @@ def test_ctr_small_files_tiny_chunks(torch, oracle, n, staged):
         src, enc = os.path.join(d, "p"), os.path.join(d, "c")
         data.tofile(src)
         for chunk, threads in ((16, 8), (64, 1), (1 << 20, 0), (4096 + 16, 5)):
-            crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=chunk, threads=threads, staged=staged)
+            crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=chunk, threads=threads, direct=direct)
             assert np.array_equal(np.fromfile(enc, np.uint8), want), (chunk, threads)
 
 
 @PATHS
-def test_ctr_in_place_same_file(torch, oracle, staged):
+def test_ctr_in_place_same_file(torch, oracle, direct):
     from paper_1403_7295_gb300.filecrypt import crypt_file, trim
 
     n = (3 << 20) + 77
@@ -75,16 +75,16 @@ def test_ctr_in_place_same_file(torch, oracle, staged):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "f")
         data.tofile(path)
-        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=1 << 20, threads=4, staged=staged)
+        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=1 << 20, threads=4, direct=direct)
         assert os.path.getsize(path) == n
         assert np.array_equal(np.fromfile(path, np.uint8), oracle.ctr_xcrypt(key, 128, iv, data))
         trim()  # the next call pins fresh buffers
-        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=(1 << 18) + 16, threads=7, staged=staged)
+        crypt_file(path, path, key, "ctr", bytes(iv), chunk_bytes=(1 << 18) + 16, threads=7, direct=direct)
         assert np.array_equal(np.fromfile(path, np.uint8), data)
 
 
 @PATHS
-def test_ecb_file_round_trip(torch, oracle, staged):
+def test_ecb_file_round_trip(torch, oracle, direct):
     from paper_1403_7295_gb300.filecrypt import crypt_file
 
     n = 12 << 20
@@ -93,11 +93,11 @@ def test_ecb_file_round_trip(torch, oracle, staged):
     with tempfile.TemporaryDirectory() as d:
         src, enc, dec = (os.path.join(d, f) for f in ("p", "c", "q"))
         data.tofile(src)
-        crypt_file(src, enc, key, "ecb-enc", chunk_bytes=5 << 20, staged=staged)
+        crypt_file(src, enc, key, "ecb-enc", chunk_bytes=5 << 20, direct=direct)
         got = np.fromfile(enc, np.uint8)
         assert np.array_equal(got[: 1 << 16], oracle.ecb_encrypt(key, 128, data[: 1 << 16]))
         assert np.array_equal(got[-(1 << 16):], oracle.ecb_encrypt(key, 128, data[-(1 << 16):]))
-        crypt_file(enc, dec, key, "ecb-dec", chunk_bytes=3 << 20, threads=5, staged=staged)
+        crypt_file(enc, dec, key, "ecb-dec", chunk_bytes=3 << 20, threads=5, direct=direct)
         assert np.array_equal(np.fromfile(dec, np.uint8), data)
         open(src, "ab").write(b"x")
         with pytest.raises(ValueError):
@@ -105,7 +105,7 @@ def test_ecb_file_round_trip(torch, oracle, staged):
 
 
 @PATHS
-def test_existing_longer_destination_is_replaced(torch, oracle, staged):
+def test_existing_longer_destination_is_replaced(torch, oracle, direct):
     """dst already holds other, longer content: afterwards it has exactly the
     source length and the cipher bytes (nothing stale past the end, nothing
     stale inside), on both paths."""
@@ -119,6 +119,6 @@ def test_existing_longer_destination_is_replaced(torch, oracle, staged):
         src, enc = os.path.join(d, "p"), os.path.join(d, "c")
         data.tofile(src)
         synth.bytes_np(76, synth.STREAM_DATA, 2 * n + 4096).tofile(enc)
-        r = crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=(1 << 20) + 16, threads=6, staged=staged)
+        r = crypt_file(src, enc, key, "ctr", bytes(iv), chunk_bytes=(1 << 20) + 16, threads=6, direct=direct)
         assert r["bytes"] == n and os.path.getsize(enc) == n
         assert np.array_equal(np.fromfile(enc, np.uint8), oracle.ctr_xcrypt(key, 256, iv, data))

@@ -4,9 +4,11 @@ AES is exact integer work with one correct output per (key, input), so the
 bar is bit-exact equality.  Cases span several CTAs and a ragged tail, every
 launch shape the library accepts, all three key sizes, ECB encrypt/decrypt
 and CTR, the 16 MiB ECB round trip, counter wrap, in-place operation, and
-canary bands around every output.  The large buffers (1 GiB, 8 GiB) use the
-default launch shape the bench times and are checked on sampled blocks the
-oracle computes one by one, plus whole-buffer properties.
+canary bands around every output.  Whole buffers of 64 MiB (every key size
+and op: past the 19 MiB where the default CTR kernel starts walking whole
+waves of counter runs) and 1 GiB are compared with the threaded oracle byte
+for byte at the default launch shape the bench times; 8 GiB is checked on
+sampled blocks the oracle computes one by one, plus whole-buffer round trips.
 """
 import ctypes
 
@@ -158,10 +160,50 @@ def sample_indices(nblocks: int, count: int, seed: int) -> np.ndarray:
     return np.unique(np.concatenate([idx, np.array([0, nblocks - 1], np.uint64)]))
 
 
-@pytest.mark.parametrize("gib", [1, 8])
-def test_full_size_sampled(A, torch, oracle, gib):
-    """1 GiB and 8 GiB buffers at the bench's launch shape: sampled blocks vs
+@pytest.mark.parametrize("bits", KEY_BITS)
+@pytest.mark.parametrize("op", ["ctr", "ecb_enc", "ecb_dec"])
+def test_whole_buffer_64MiB(A, torch, oracle, bits, op):
+    """64 MiB (2^22 blocks = 16,384 counter runs, over three whole waves of
+    the default CTR kernel's 4,864 warps plus a split tail) at the default
+    launch shape, every byte against the threaded oracle; the counter start
+    is not run-aligned, so the first and last runs are partial."""
+    n = 64 << 20
+    seed = 61 + bits + len(op)
+    key = synth.key_bytes(seed, bits)
+    iv = synth.iv_bytes(seed, counter0=0x00ABCD37)
+    x = synth.bytes_np(seed, synth.STREAM_DATA, n)
+    ks = A.aes_expand_key(key)
+    g = Guarded(n)
+    run_op(A, op, ks, iv, to_dev(x), g.view)
+    torch.cuda.synchronize()
+    assert np.array_equal(g.numpy(), oracle_op(oracle, op, key, bits, iv, x, nthreads=host_threads()))
+    assert g.intact()
+
+
+@pytest.mark.parametrize("bits,op", [(128, "ctr"), (256, "ctr"), (128, "ecb_enc"), (128, "ecb_dec")])
+def test_whole_buffer_1GiB(A, torch, oracle, bits, op):
+    """1 GiB at the bench's launch shape, every byte against the threaded
+    oracle (AES-128 CTR is the bench's headline kernel; the other key size and
+    both ECB directions take the other kernels)."""
+    n = 1 << 30
+    seed = 41 + bits
+    key = synth.key_bytes(seed, bits)
+    iv = synth.iv_bytes(seed)
+    ks = A.aes_expand_key(key)
+    x = synth.bytes_torch(seed, synth.STREAM_DATA, n, device="cuda")
+    y = run_op(A, op, ks, iv, x)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    del y
+    want = oracle_op(oracle, op, key, bits, iv, x.cpu().numpy(), nthreads=host_threads())
+    mism = np.flatnonzero(got != want)
+    assert mism.size == 0, f"{mism.size} bytes differ, first at {mism[:4]}"
+
+
+def test_full_size_sampled_8GiB(A, torch, oracle):
+    """8 GiB (the bench's buffer) at its launch shape: 4,096 sampled blocks vs
     the oracle (one by one), whole-buffer round trips on the device."""
+    gib = 8
     n = gib << 30
     nblocks = n // 16
     seed = 40 + gib

@@ -159,7 +159,8 @@ def test_file_crypt_validation_and_empty_file(lib, tmp_path):
     assert L.aes_file_crypt(s, d, 3, kr, ivb, None, None) == 1                     # unknown mode
     assert L.aes_file_crypt(s, d, 0, kr, None, None, None) == 1                    # CTR without IV
     assert L.aes_file_crypt(s, d, 0, None, ivb, None, None) == 1                   # no key
-    for cfg in (F.FileConfig(17, 0, 0), F.FileConfig(0, 65, 0), F.FileConfig(0, -1, 0), F.FileConfig(0, 0, 2)):
+    for cfg in (F.FileConfig(17, 0, 0), F.FileConfig(0, 65, 0), F.FileConfig(0, -1, 0), F.FileConfig(0, 0, 4),
+                F.FileConfig(0, 0, F.STAGED | F.DIRECT)):
         assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(cfg), None) == 1
     missing = os.fsencode(tmp_path / "missing")
     assert L.aes_file_crypt(missing, d, 0, kr, ivb, None, ctypes.byref(st)) == 11
@@ -170,8 +171,9 @@ def test_file_crypt_validation_and_empty_file(lib, tmp_path):
     src.write_bytes(b"")
     assert L.aes_file_crypt(s, d, 0, kr, ivb, None, ctypes.byref(st)) == 0
     assert dst.exists() and dst.stat().st_size == 0 and st.bytes == 0 and st.chunks == 0 and st.direct == 0
-    staged = F.FileConfig(0, 0, F.STAGED)  # a known flag: accepted
-    assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(staged), None) == 0
+    for flag in (F.STAGED, F.DIRECT):  # the known flags, one at a time: accepted
+        cfg = F.FileConfig(0, 0, flag)
+        assert L.aes_file_crypt(s, d, 0, kr, ivb, ctypes.byref(cfg), None) == 0
     L.aes_file_trim()  # nothing pinned yet: a no-op without a GPU
 
 
@@ -196,3 +198,33 @@ def test_server_validation_without_a_gpu(lib):
     assert L.aes_server_healthy(None) == 0 and L.aes_server_idle(None) == 0
     assert L.aes_server_output(None) is None
     L.aes_server_destroy(None)
+
+
+def test_ctr_iv_advance_is_the_counter_block_function(lib):
+    """aes_ctr_iv_advance: SP 800-38A §6.5 counter blocks, the 32-bit
+    big-endian counter in bytes 12..15 advanced modulo 2^32, the nonce bytes
+    untouched (written out here from the definition), in place too."""
+    rng = np.random.default_rng(1403)
+    cases = [(bytes(12) + b"\xff\xff\xff\xff", 1), (bytes(range(16)), 0), (b"\xaa" * 12 + b"\xff\xff\xff\xf0", 17),
+             (bytes(16), (1 << 32) + 5), (bytes(16), (1 << 64) - 1)]
+    cases += [(rng.integers(0, 256, 16, dtype=np.uint8).tobytes(), int(rng.integers(0, 1 << 62))) for _ in range(200)]
+    for iv, b in cases:
+        c0 = int.from_bytes(iv[12:], "big")
+        want = iv[:12] + ((c0 + b) % (1 << 32)).to_bytes(4, "big")
+        assert A.aes_ctr_iv_advance(iv, b) == want, (iv.hex(), b)
+        buf = (ctypes.c_uint8 * 16).from_buffer_copy(iv)
+        assert lib.aes_ctr_iv_advance(buf, b, buf) == 0  # the same array in and out
+        assert bytes(buf) == want
+    out = (ctypes.c_uint8 * 16)()
+    assert lib.aes_ctr_iv_advance(None, 1, out) == 1
+    assert lib.aes_ctr_iv_advance(out, 1, None) == 1
+
+
+def test_xts_key_sizes_refused_before_any_gpu_work(lib):
+    """XTS is defined for AES-128 and AES-256 key pairs (IEEE 1619); a 192-bit
+    or mixed pair is refused on the host (the pointers are never touched)."""
+    ks = {b: A.aes_expand_key(synth.key_bytes(3, b)) for b in (128, 192, 256)}
+    p = 1 << 20  # never dereferenced
+    for d, t in ((192, 192), (128, 256), (256, 128), (192, 128), (128, 192)):
+        for fn in (lib.aes_xts_encrypt, lib.aes_xts_decrypt):
+            assert fn(ctypes.byref(ks[d]), ctypes.byref(ks[t]), 0, 512, p, p, 4096, None) == 2

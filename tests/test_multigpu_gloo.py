@@ -20,6 +20,15 @@ torch = pytest.importorskip("torch")
 dist = pytest.importorskip("torch.distributed")
 
 
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    """The shard IVs come from the library's aes_ctr_iv_advance (a host call:
+    no GPU needed); build it once here, before the ranks start."""
+    from paper_1403_7295_gb300 import build
+
+    build.build()
+
+
 def _free_port() -> int:
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))

@@ -346,6 +346,54 @@ def test_chunked_equals_single_pass(oracle, threads, n):
         assert np.array_equal(oracle.ecb_decrypt(key, 256, e1, nthreads=threads), data)
 
 
+@pytest.mark.parametrize("threads", [1, 7])
+def test_message_list_matches_openssl_per_message(oracle, threads):
+    """ref_batch_mt (a list of messages over threads, the batched workloads'
+    checker) against OpenSSL message by message: CTR and PKCS#7 + ECB, every
+    key size, empty and ragged lengths, then decryption back with the padding
+    checked, a corrupted pad and a bad key size reported per message."""
+    padding = pytest.importorskip("cryptography.hazmat.primitives.padding")
+    n = 60
+    lengths = np.array([0, 1, 15, 16, 17, 31, 32, 33] + [int(x) for x in
+                       synth.uniform01(3, synth.STREAM_LENGTH, n - 8) * 700], np.uint64)
+    kb = np.array([128, 192, 256], np.uint32)[np.arange(n) % 3]
+    keys = synth.bytes_np(3, synth.STREAM_KEY, 32 * n).reshape(n, 32)
+    ivs = synth.bytes_np(3, synth.STREAM_NONCE, 16 * n).reshape(n, 16).copy()
+    ivs[:, 12:] = 0  # OpenSSL carries into the nonce on a wrap; start low
+    in_off = np.concatenate([[0], np.cumsum((lengths + np.uint64(15)) // np.uint64(16) * np.uint64(16))[:-1]])
+    in_off = in_off.astype(np.uint64)
+    total = int(in_off[-1] + lengths[-1] + np.uint64(16))
+    data = synth.bytes_np(3, synth.STREAM_DATA, total)
+    ct_len = lengths - lengths % np.uint64(16) + np.uint64(16)
+    out_off = np.concatenate([[0], np.cumsum(ct_len)[:-1]]).astype(np.uint64)
+    out_size = int(ct_len.sum())
+    ctr, ctr_len, st = oracle.batch(0, data, in_off, lengths, out_size, out_off, keys, kb, ivs, nthreads=threads)
+    assert np.all(st == 0) and np.array_equal(ctr_len, lengths)
+    enc, enc_len, st = oracle.batch(1, data, in_off, lengths, out_size, out_off, keys, kb, nthreads=threads)
+    assert np.all(st == 0) and np.array_equal(enc_len, ct_len)
+    for m in range(n):
+        key, ln = keys[m][: kb[m] // 8], int(lengths[m])
+        msg = data[int(in_off[m]): int(in_off[m]) + ln]
+        o = int(out_off[m])
+        assert np.array_equal(ctr[o: o + ln], openssl_ctr(key, ivs[m], msg)), m
+        p = padding.PKCS7(128).padder()
+        padded = p.update(bytes(msg)) + p.finalize()
+        assert np.array_equal(enc[o: o + int(ct_len[m])], openssl_ecb(key, padded)), m
+    enc[int(out_off[5]) + int(ct_len[5]) - 1] ^= 0x5A  # corrupt message 5's last ciphertext byte
+    kb2 = kb.copy()
+    kb2[7] = 100
+    dec, dec_len, st = oracle.batch(2, enc, out_off, ct_len, out_size, out_off, keys, kb2, nthreads=threads)
+    for m in range(n):
+        if m == 7:
+            assert st[m] == -1 and dec_len[m] == 0   # REF_ERR_KEYSIZE
+        elif m == 5:
+            assert st[m] == -3 and dec_len[m] == 0   # REF_ERR_PADDING (a random last block passes ~2^-8 of the time; this seeded one fails)
+        else:
+            o, ln = int(out_off[m]), int(lengths[m])
+            assert st[m] == 0 and dec_len[m] == ln
+            assert np.array_equal(dec[o: o + ln], data[int(in_off[m]): int(in_off[m]) + ln]), m
+
+
 def test_ecb_length_rejected(oracle):
     with pytest.raises(ValueError):
         oracle.ecb_encrypt(np.zeros(16, np.uint8), 128, np.zeros(17, np.uint8))

@@ -6,9 +6,10 @@ stall other streams, or inside a framework that owns every device
 allocation.  ``aes_batch_submit_noalloc`` serves them by keeping the batch
 workspace in a fixed device array of the library.  These tests call it
 through the C ABI for two different batches in a row (then the first one
-again, over the array the second left behind) and compare every output byte,
-status and output length with the workspace-taking ``aes_batch_submit``
-(AES is exact, so the tolerance is zero), and check the size limit.
+again, over the array the second left behind), and for a batch of exactly
+the message cap twice, and compare every output byte, status and output
+length with the workspace-taking ``aes_batch_submit`` (AES is exact, so the
+tolerance is zero), and check the size limit.
 
 This file sorts last so a run that stops at the first failure has already run
 everything else; it also passes on its own in a fresh process.
@@ -91,6 +92,33 @@ def test_noalloc_matches_workspace_call_two_calls_in_a_row(torch, lib):
     torch.cuda.synchronize()
     for g, r in zip(snapshot(b1), refs[0]):
         assert torch.equal(g, r)
+
+
+def test_noalloc_at_the_message_cap(torch, lib):
+    """Exactly AES_BATCH_NOALLOC_MAX_MSGS (65,536) messages, so the scratch
+    array is used to its last byte (offsets, 16 scan chunks, counters): two
+    calls in a row equal aes_batch_submit."""
+    from paper_1403_7295_gb300 import batch as B
+
+    n = 65536
+    lengths = W.uniform_lengths(4, n, 0, 600)
+    lengths[:4] = [0, 1, 16, 8192]  # empty, one byte, one block, a tile-phase message
+    in_off, total = B.pack_offsets(lengths)
+    data = synth.bytes_torch(4, synth.STREAM_DATA, max(total, 16), device="cuda")
+    b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=W.message_keys(4, n),
+                key_bits=W.key_sizes(4, n), ivs=W.message_ivs(4, n, counter0=0xFFFFFF80))
+    reset(b)
+    b.submit()
+    torch.cuda.synchronize()
+    ref = snapshot(b)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        reset(b)
+        assert lib.aes_batch_submit_noalloc(ctypes.byref(b.desc), stream) == 0
+        torch.cuda.synchronize()
+        for g, r in zip(snapshot(b), ref):
+            assert torch.equal(g, r)
+    assert int((b.status != 0).sum()) == 0
 
 
 def test_noalloc_size_limit_and_arguments(torch, lib):
