@@ -863,9 +863,34 @@ constexpr bool region_fits() {
 static_assert(region_fits<kBatchCtr>() && region_fits<kBatchEcbEnc>() && region_fits<kBatchEcbDec>(),
               "short-phase groups exceed a warp's share of the window region");
 
+// A lane's current message in the short phase, kept in registers while the
+// lane's blocks stay in it: its record and, for CTR, the cached counter run
+// (run, xr, c10) and that run's round-2 columns d, so a block in the cached
+// run reads no per-message word from shared memory.
+struct ShortCur {
+  GroupMsg r;
+  uint32_t run, xr, c10;
+  uint4 d;
+};
+
+template <int OPB>
+__device__ __forceinline__ void load_short_cur(const uint32_t* wrk, const GroupMsg* rec, uint32_t ci,
+                                               ShortCur& c) {
+  c.r = rec[ci];
+  if (OPB == kBatchCtr) {
+    const uint32_t* rk = wrk + (c.r.info >> 16) * kShortStride<OPB>;
+    const uint4 q = lds128(rk + kRunWords);  // rk0 word 3, cached run, xr, c10
+    c.run = q.y;
+    c.xr = q.z;
+    c.c10 = q.w;
+    c.d = lds128(rk + kRunD);
+  }
+}
+
 template <int OPB>
 __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, const uint32_t* wrk,
-                                            const GroupMsg& r, uint32_t gr, unsigned long long m0) {
+                                            const ShortCur& c, uint32_t gr, unsigned long long m0) {
+  const GroupMsg& r = c.r;
   const uint32_t nr = r.info & 0xFFu, rem = (r.info >> 8) & 0xFFu, j = r.info >> 16;
   const uint32_t* rk = wrk + j * kShortStride<OPB>;
   const bool full = gr < r.full_end;
@@ -878,18 +903,17 @@ __device__ __forceinline__ void short_block(const BatchArgs& a, const Tabs& T, c
     v = load_partial(src, rem);
   if (OPB == kBatchCtr) {
     const uint32_t ctr = r.ctr0 + gr;
-    const uint4 q = lds128(rk + kRunWords);  // rk0 word 3, cached run, xr, c10
-    uint32_t xr = q.z;
-    uint4 d = lds128(rk + kRunD);
-    if ((ctr >> 8) != q.y) {  // outside the cached run: that run's constants (15 lookups)
-      xr = __byte_perm(ctr & ~255u, 0, 0x0123) ^ q.x;
+    uint32_t xr = c.xr;
+    uint4 d = c.d;
+    if ((ctr >> 8) != c.run) {  // outside the cached run: that run's constants (15 lookups)
+      xr = __byte_perm(ctr & ~255u, 0, 0x0123) ^ rk[kCtrRk0w3];
       const uint4 c1 = lds128(rk + kCtrC1), k2 = lds128(rk + 8);
       const uint32_t s1 = c1.y ^ T.t2(xr), s2 = c1.z ^ T.t1(xr), s3 = c1.w ^ T.t0(xr);
       d = make_uint4(k2.x ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3), k2.y ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3),
                      k2.z ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1), k2.w ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2));
     }
     // rounds 1-2: only round-1 column 0 depends on the counter's low byte
-    const uint32_t s0 = q.w ^ T.t3(xr ^ ((ctr & 255u) << 24));
+    const uint32_t s0 = c.c10 ^ T.t3(xr ^ ((ctr & 255u) << 24));
     State s{d.x ^ T.t0(s0), d.y ^ T.t3(s0), d.z ^ T.t2(s0), d.w ^ T.t1(s0)};
     s = enc_lanes(T, s, rk, nr, 3);
     const uint4 o = make_uint4(v.x ^ s.s0, v.y ^ s.s1, v.z ^ s.s2, v.w ^ s.s3);
@@ -1053,7 +1077,7 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
     const uint32_t ng = __popc(valid);
     const uint32_t my_first = lane < ng ? first[lane] : 0xFFFFFFFFu;
     uint32_t cur = 0xFFFFFFFFu;
-    GroupMsg r{};
+    ShortCur sc{};
 #pragma unroll 1
     for (uint32_t base = 0; base < nblk; base += 32) {
       const uint32_t gr = base + lane;
@@ -1065,9 +1089,9 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       if (gr < nblk) {
         if (ci != cur) {
           cur = ci;
-          r = rec[ci];
+          load_short_cur<OPB>(wrk, rec, ci, sc);
         }
-        short_block<OPB>(a, T, wrk, r, gr, m0);
+        short_block<OPB>(a, T, wrk, sc, gr, m0);
       }
     }
     __syncwarp();  // the slots are refilled next
