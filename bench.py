@@ -51,7 +51,7 @@ def parse_args():
     p.add_argument("--bits", type=int, default=128, choices=[128, 192, 256])
     p.add_argument("--mode", default="ctr", choices=["ctr", "ecb_enc", "ecb_dec"])
     p.add_argument("--size-mib", type=int, default=8192)
-    p.add_argument("--variant", type=int, default=0, help="0 auto, 1 T-table, 2 bitsliced")
+    p.add_argument("--variant", type=int, default=0, help="0 auto, 1 T-table, 2 bitsliced, 3 T-table with TMA-staged input (CTR)")
     p.add_argument("--cta", type=int, default=0)
     p.add_argument("--bpt", type=int, default=0)
     p.add_argument("--sweep", action="store_true", help="also time the 36-run key/mode/size sweep")
@@ -477,8 +477,8 @@ def executed_lookups_per_block(args, bits, nbytes):
 # with the sources whose hash it records (numbers from a stale summary are
 # not used).
 PROFILE_OF_VARIANT = {
-    0: ("ttable_ctr_aes128_1GiB.md", ["aes_ttable.cuh"]),
-    1: ("ttable_ctr_aes128_1GiB.md", ["aes_ttable.cuh"]),
+    0: ("ttable_ctr_aes128_8GiB.md", ["aes_ttable.cuh"]),
+    1: ("ttable_ctr_aes128_8GiB.md", ["aes_ttable.cuh"]),
     2: ("bitslice_ctr_aes128_256MiB.md", ["aes_bitslice.cu", "aes_bitslice_circuit.cuh"]),
 }
 
@@ -531,14 +531,31 @@ def modes_arm(torch, A, x, y):
 
 
 def variant_arm(torch, A, args, ks, iv, x, y, ttable_gbps):
-    """The two round implementations on the headline workload: the library's
-    choice (T-tables) against the bitsliced circuit."""
+    """The round implementations on the headline workload: the library's
+    choice (T-tables) against the bitsliced circuit; for CTR also the
+    T-table kernel with TMA-staged input against the default's plain loads,
+    at the headline size and at 1 GiB, timed back to back."""
     cfg = dict(variant=2, cta_threads=0, blocks_per_thread=0, grid_ctas=0)
     steps = max(10, args.steps // 10)
     ms = time_device(torch, lambda: launch(A, args.mode, ks, iv, x, y, cfg), steps, 3)
     bs = x.numel() * steps / (ms / 1e3) / 1e9
-    return {"ttable_gbps": round(ttable_gbps, 1), "bitslice_gbps": round(bs, 1),
-            "chosen": "ttable" if ttable_gbps >= bs else "bitslice"}
+    out = {"ttable_gbps": round(ttable_gbps, 1), "bitslice_gbps": round(bs, 1),
+           "chosen": "ttable" if ttable_gbps >= bs else "bitslice"}
+    if args.mode == "ctr" and not args.variant and not args.cta and not args.bpt:
+        bulk = dict(variant=3, cta_threads=0, blocks_per_thread=0, grid_ctas=0)
+        tma = {}
+        for n in sorted({x.numel(), min(1 << 30, x.numel())}):
+            xs, ys = x[:n], y[:n]
+            k = max(10, int(20 * (8 << 30) / n) // 10)
+            g = {}
+            for name, c in (("default_plain_loads", None), ("tma_bulk_staged", bulk),
+                            ("default_plain_loads_again", None)):
+                t = time_device(torch, lambda: A.aes_ctr_xcrypt(ks, iv, xs, ys, config=c), k, 3)
+                g[name] = round(n * k / (t / 1e3) / 1e9, 1)
+            tma[f"{n >> 20}_MiB"] = g
+        out["tma_staging"] = tma
+        out["tma_wait_timeouts"] = A.aes_take_wait_timeouts()
+    return out
 
 
 def e2e_arm(torch, A, args, ks, iv, nbytes, cfg):

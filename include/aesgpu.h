@@ -68,7 +68,11 @@ typedef struct aes_key_schedule {
 typedef enum aes_variant {
     AES_VARIANT_AUTO = 0,     /* the library's measured choice per call */
     AES_VARIANT_TTABLE = 1,   /* shared-memory T-tables, replicated per bank */
-    AES_VARIANT_BITSLICE = 2  /* bitsliced S-box / MixColumns on LOP3 */
+    AES_VARIANT_BITSLICE = 2, /* bitsliced S-box / MixColumns on LOP3 */
+    AES_VARIANT_TTABLE_BULK = 3 /* CTR only: the run-cached T-table kernel with each half run of
+                                   input (2 KiB) staged into shared memory by a TMA bulk copy that
+                                   overlaps the rounds; kept as the measured alternative to the
+                                   default's plain 128-bit loads (other modes: AES_ERR_ARG) */
 } aes_variant;
 
 /* Optional launch shape for the _ex calls; a zero field means "choose". */
@@ -451,6 +455,16 @@ aes_status aes_server_replay(aes_server *s, uint64_t n, const double *arrival_s,
                              const uint64_t *in_offs, const uint64_t *lengths, double time_limit_s,
                              double *latency_s, double *wait_s, uint32_t *counters, void *capture,
                              const uint64_t *capture_off);
+
+/* Device waits that gave up: the TMA-staged CTR variant (AES_VARIANT_TTABLE_BULK)
+ * bounds each wait for its staged copy to about a second of SM clock; a warp
+ * whose copy has not landed by then counts one timeout, leaves its remaining
+ * blocks unwritten and stops.  *count gets the timeouts counted on the current
+ * device since the last call, and the count restarts at 0.  Synchronous (it
+ * reads a device word): call it once the work it covers has completed.
+ * Returns AES_OK, AES_ERR_TIMEOUT when *count > 0, AES_ERR_ARG for a null
+ * pointer or AES_ERR_CUDA. */
+aes_status aes_take_wait_timeouts(uint32_t *count);
 
 /* The CUDA error code behind the calling thread's last AES_ERR_CUDA (0 if none). */
 int aes_last_cuda_error(void);

@@ -21,7 +21,7 @@ STATUS_NAMES = {
     5: "AES_ERR_OVERLAP", 6: "AES_ERR_PADDING", 7: "AES_ERR_NOMEM", 8: "AES_ERR_CUDA",
     9: "AES_ERR_TIMEOUT", 10: "AES_ERR_BUSY",
 }
-VARIANT_AUTO, VARIANT_TTABLE, VARIANT_BITSLICE = 0, 1, 2
+VARIANT_AUTO, VARIANT_TTABLE, VARIANT_BITSLICE, VARIANT_TTABLE_BULK = 0, 1, 2, 3
 
 
 class AesError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
             getattr(L, name).argtypes = [ksp, ksp, ctypes.c_uint64, sz, vp, vp, sz, vp]
             getattr(L, name).restype = ctypes.c_int
         L.aes_cbc_decrypt.restype = ctypes.c_int
+        L.aes_take_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+        L.aes_take_wait_timeouts.restype = ctypes.c_int
         L.aes_last_cuda_error.argtypes = []
         L.aes_status_string.argtypes = [ctypes.c_int]
         L.aes_status_string.restype = ctypes.c_char_p
@@ -185,6 +187,16 @@ def aes_ctr_iv_advance(iv, first_block: int) -> bytes:
     _check(lib().aes_ctr_iv_advance(ctypes.cast(vb, ctypes.c_void_p), first_block,
                                     ctypes.cast(out, ctypes.c_void_p)), "aes_ctr_iv_advance")
     return bytes(out)
+
+
+def aes_take_wait_timeouts() -> int:
+    """Bounded device waits (of the TMA-staged CTR variant) that gave up on
+    the current device since the last call; the count restarts at 0."""
+    n = ctypes.c_uint32(0)
+    rc = lib().aes_take_wait_timeouts(ctypes.byref(n))
+    if rc not in (AES_OK, 9):  # 9: AES_ERR_TIMEOUT, reported through the count
+        _check(rc, "aes_take_wait_timeouts")
+    return int(n.value)
 
 
 def aes_cbc_decrypt(ks: KeySchedule, iv, inp, out=None, stream=None):

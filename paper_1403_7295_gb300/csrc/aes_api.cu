@@ -148,6 +148,15 @@ aes_status resolve_shape(Op op, int nr, uint64_t nblocks, const aes_launch_confi
     *shape = LaunchShape{kBitsliceThreads, 16, grid};
     return AES_OK;
   }
+  if (variant == AES_VARIANT_TTABLE_BULK) {
+    // CTR only, the run-cached layout (blocks_per_thread 0); any CTA size
+    if (op != Op::kCtr || (cfg && cfg->blocks_per_thread != 0)) return AES_ERR_ARG;
+    const int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : 1024;
+    const int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
+    if (cta < 128 || cta > 1024 || cta % 32 != 0 || grid < 0) return AES_ERR_ARG;
+    *shape = LaunchShape{cta, 0, grid};
+    return AES_OK;
+  }
   if (variant != AES_VARIANT_AUTO && variant != AES_VARIANT_TTABLE) return AES_ERR_ARG;
   int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : d.cta_threads;
   int bpt = (cfg && cfg->blocks_per_thread) ? cfg->blocks_per_thread : d.blocks_per_thread;
@@ -205,7 +214,7 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
   if (op == Op::kCtr && iv == nullptr) return AES_ERR_ARG;
   if (op != Op::kCtr && nbytes % 16 != 0) return AES_ERR_LENGTH;
   if (cfg && cfg->variant != AES_VARIANT_AUTO && cfg->variant != AES_VARIANT_TTABLE &&
-      cfg->variant != AES_VARIANT_BITSLICE)
+      cfg->variant != AES_VARIANT_BITSLICE && cfg->variant != AES_VARIANT_TTABLE_BULK)
     return AES_ERR_ARG;
   if (nbytes == 0) return AES_OK;
   const void* din = nullptr;
@@ -230,6 +239,10 @@ aes_status run(Op op, const aes_key_schedule* ks, const uint8_t* iv, const void*
     e = launch_bitslice(op, nr, din, dout, nblocks, tail, rk, cp, shape, st);
     if (e != cudaSuccess) return cuda_failure(e);
     return AES_OK;
+  }
+  if (cfg && cfg->variant == AES_VARIANT_TTABLE_BULK) {
+    e = launch_ttable_ctr_bulk(nr, din, dout, nblocks, tail, rk, cp, shape, st);
+    return e == cudaSuccess ? AES_OK : cuda_failure(e);
   }
   switch (op) {
     case Op::kEcbEncrypt: e = launch_ttable_enc(nr, din, dout, nblocks, 0, rk, cp, shape, st); break;
@@ -482,6 +495,15 @@ aes_status aes_batch_submit_ex(const aes_batch* b, void* d_workspace, size_t wor
 aes_status aes_batch_submit(const aes_batch* b, void* d_workspace, size_t workspace_bytes,
                             void* stream) {
   return batch_submit(b, d_workspace, workspace_bytes, stream, nullptr);
+}
+
+aes_status aes_take_wait_timeouts(uint32_t* count) {
+  if (count == nullptr) return AES_ERR_ARG;
+  unsigned int v = 0;
+  const cudaError_t e = take_bulk_timeouts(&v);
+  if (e != cudaSuccess) return cuda_failure(e);
+  *count = v;
+  return v ? AES_ERR_TIMEOUT : AES_OK;
 }
 
 int aes_last_cuda_error(void) { return g_last_cuda_error; }

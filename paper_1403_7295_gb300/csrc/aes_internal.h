@@ -44,7 +44,11 @@ struct LaunchShape {
 AESGPU_DECLARE_LAUNCH(launch_ttable_enc)
 AESGPU_DECLARE_LAUNCH(launch_ttable_dec)
 AESGPU_DECLARE_LAUNCH(launch_ttable_ctr)
+AESGPU_DECLARE_LAUNCH(launch_ttable_ctr_bulk)  // CTR with TMA-staged input (cta_threads from the shape)
 #undef AESGPU_DECLARE_LAUNCH
+// Given-up bounded waits of the TMA-staged kernel on the current device since
+// the last call (then reset); synchronises with the device.
+cudaError_t take_bulk_timeouts(unsigned int* out);
 
 // Bitsliced launches (32 blocks per thread, 128-thread CTAs).  Decryption takes
 // the encryption schedule (plain InvCipher order).

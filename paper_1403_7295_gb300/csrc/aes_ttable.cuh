@@ -315,5 +315,134 @@ __global__ void __launch_bounds__(1024, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged variant of the run-cached CTR kernel (AES_VARIANT_TTABLE_BULK).
+//
+// The same rounds and counter-run caching, but each half run of input (128
+// blocks, 2 KiB) is brought into a per-warp shared-memory buffer by one
+// cp.async.bulk copy (the TMA engine, no LSU instructions) issued before the
+// half run's keystream is computed, so the copy overlaps the rounds; the
+// lanes then read their blocks from shared memory (LDS.128), XOR and store.
+// Runs not wholly inside the buffer, and the split tail pieces, take the
+// plain loads of ctr_run_steps.  No cluster, no multicast: every copy reads
+// this GPU's own buffer into the issuing CTA's shared memory.
+//
+// Each wait on the buffer's mbarrier is bounded (about a second of SM
+// clock): a warp whose copy has not landed by then counts the timeout in
+// *timeouts, waits (again bounded) for its copy to finish, writes nothing
+// more and returns.
+constexpr uint32_t kBulkHalf = 128;                   // blocks per staged copy
+constexpr uint32_t kBulkBytes = kBulkHalf * 16;       // 2 KiB per warp
+__host__ __device__ constexpr int bulk_smem_bytes(int warps) {
+  return kTtableSmemEnc + warps * static_cast<int>(kBulkBytes) + warps * 8;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// true once the mbarrier's phase with parity `parity` has completed, false
+// after `limit` SM clocks
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(1024, 1)
+    ttable_ctr_bulk_kernel(const uint4* in, uint4* out, uint64_t nblocks, uint32_t tail_bytes,
+                           const __grid_constant__ RoundKeys rk, const __grid_constant__ CtrParams cp,
+                           unsigned int* timeouts) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  constexpr long long kWaitLimit = 2000000000ll;  // SM clocks, ~1 s at 2 GHz
+  pdl_launch_dependents();
+  fill_tables<false>(smem);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  char* stage_p = reinterpret_cast<char*>(smem) + kTtableSmemEnc + warp * kBulkBytes;
+  const uint32_t stage = smem_addr(stage_p);
+  const uint32_t mbar = smem_addr(reinterpret_cast<char*>(smem) + kTtableSmemEnc + nwarps * kBulkBytes) + 8 * warp;
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait_previous();  // the caller's buffers are touched only after this point
+  const char* base = reinterpret_cast<const char*>(smem);
+  const Tabs T{base, base + kRegionB, base + kRegionC, lane * 4, lane * 4 + 128};
+
+  const uint32_t off0 = cp.ctr0 & 255u;
+  const uint64_t units = nblocks + (tail_bytes ? 1 : 0);
+  const uint64_t runs = (units + off0 + 255) / 256;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * nwarps;
+  const uint64_t wid = static_cast<uint64_t>(blockIdx.x) * nwarps + warp;
+  const uint64_t whole = cp.whole_runs;
+  uint32_t parity = 0;
+  for (uint64_t run = wid; run < whole; run += warps) {
+    const int64_t first = static_cast<int64_t>(run) * 256 - off0;
+    if (first < 0 || static_cast<uint64_t>(first) + 256 > nblocks) {  // a partial run: plain loads
+      ctr_run_steps<NR, true>(T, in, out, nblocks, units, tail_bytes, rk, cp, off0, run, 0, 8, lane);
+      continue;
+    }
+    const uint32_t ctr_run = (cp.ctr0 & ~255u) + static_cast<uint32_t>(run) * 256u;
+    const uint32_t xr = __byte_perm(ctr_run, 0, 0x0123) ^ cp.rk0w3;
+    const uint32_t s1 = cp.c1[1] ^ T.t2(xr), s2 = cp.c1[2] ^ T.t1(xr), s3 = cp.c1[3] ^ T.t0(xr);
+    const uint32_t d0 = rk.w[8] ^ T.t1(s1) ^ T.t2(s2) ^ T.t3(s3);
+    const uint32_t d1 = rk.w[9] ^ T.t0(s1) ^ T.t1(s2) ^ T.t2(s3);
+    const uint32_t d2 = rk.w[10] ^ T.t0(s2) ^ T.t1(s3) ^ T.t3(s1);
+    const uint32_t d3 = rk.w[11] ^ T.t0(s3) ^ T.t2(s1) ^ T.t3(s2);
+#pragma unroll 1
+    for (uint32_t h = 0; h < 2; ++h) {
+      const uint4* src = in + first + kBulkHalf * h;
+      __syncwarp();  // every lane's reads of the previous half are done
+      if (lane == 0) {
+        // order those generic-proxy reads before the copy's async-proxy writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(kBulkBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(stage),
+            "l"(src), "r"(kBulkBytes), "r"(mbar)
+            : "memory");
+      }
+      State ks[4];
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        const uint32_t t = 32 * (4 * h + j) + lane;
+        const uint32_t x0 = cp.c1[0] ^ T.t3(xr ^ (t << 24));
+        State s{d0 ^ T.t0(x0), d1 ^ T.t3(x0), d2 ^ T.t2(x0), d3 ^ T.t1(x0)};
+        encrypt_rounds<NR>(T, s, rk, 3);
+        ks[j] = s;
+      }
+      if (!mbar_wait_bounded(mbar, parity, kWaitLimit)) {
+        if (lane == 0) atomicAdd(timeouts, 1u);
+        mbar_wait_bounded(mbar, parity, kWaitLimit);  // let the copy finish before the warp leaves
+        return;
+      }
+      parity ^= 1u;
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        const uint4 v = *reinterpret_cast<const uint4*>(stage_p + 16 * (32 * j + lane));
+        __stcs(out + first + kBulkHalf * h + 32 * j + lane, xor4(v, ks[j]));
+      }
+    }
+  }
+  const uint32_t shift = cp.tail_shift, steps = 8u >> shift;
+  for (uint64_t piece = wid; piece < ((runs - whole) << shift); piece += warps) {
+    const uint32_t k0 = (static_cast<uint32_t>(piece) & ((1u << shift) - 1)) * steps;
+    ctr_run_steps<NR, false>(T, in, out, nblocks, units, tail_bytes, rk, cp, off0, whole + (piece >> shift),
+                             k0, k0 + steps, lane);
+  }
+}
+
 }  // namespace
 }  // namespace aesgpu

@@ -8,6 +8,24 @@
 namespace aesgpu {
 namespace {
 
+// The grid of the run-cached CTR kernels and their run split (CtrParams).
+inline uint64_t ctr_cached_grid(uint64_t nblocks, uint32_t tail, const LaunchShape& shape, CtrParams* p) {
+  // one warp per run of 256 blocks, or per piece of a run when the runs do
+  // not fill the grid's warps: no more CTAs than those work units need
+  const uint64_t runs = (nblocks + (tail ? 1 : 0) + (p->ctr0 & 255u) + 255) / 256;
+  const uint64_t warps_per_cta = shape.cta_threads / 32;
+  uint64_t grid = shape.grid_ctas;
+  const uint64_t max_warps = grid * warps_per_cta;
+  const uint64_t work = runs >= max_warps ? max_warps : runs * ctr_tail_pieces(runs, max_warps);
+  const uint64_t needed = (work + warps_per_cta - 1) / warps_per_cta;
+  if (grid > needed) grid = needed > 0 ? needed : 1;
+  const uint64_t warps = grid * warps_per_cta;
+  p->whole_runs = runs - runs % warps;
+  const uint32_t pieces = ctr_tail_pieces(runs - p->whole_runs, warps);
+  p->tail_shift = pieces == 8 ? 3 : pieces == 4 ? 2 : pieces == 2 ? 1 : 0;
+  return grid;
+}
+
 template <int NR>
 cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint32_t tail,
                               const RoundKeys& rk, const CtrParams& cp, const LaunchShape& shape,
@@ -15,22 +33,25 @@ cudaError_t launch_ctr_cached(const void* in, void* out, uint64_t nblocks, uint3
   auto kern = ttable_ctr_cached_kernel<NR>;
   cudaError_t e = ensure_dynamic_smem(kern, kTtableSmemEnc);
   if (e != cudaSuccess) return e;
-  // one warp per run of 256 blocks, or per piece of a run when the runs do
-  // not fill the grid's warps: no more CTAs than those work units need
-  const uint64_t runs = (nblocks + (tail ? 1 : 0) + (cp.ctr0 & 255u) + 255) / 256;
-  const uint64_t warps_per_cta = shape.cta_threads / 32;
-  uint64_t grid = shape.grid_ctas;
-  const uint64_t max_warps = grid * warps_per_cta;
-  const uint64_t work = runs >= max_warps ? max_warps : runs * ctr_tail_pieces(runs, max_warps);
-  const uint64_t needed = (work + warps_per_cta - 1) / warps_per_cta;
-  if (grid > needed) grid = needed > 0 ? needed : 1;
   CtrParams p = cp;
-  const uint64_t warps = grid * warps_per_cta;
-  p.whole_runs = runs - runs % warps;
-  const uint32_t pieces = ctr_tail_pieces(runs - p.whole_runs, warps);
-  p.tail_shift = pieces == 8 ? 3 : pieces == 4 ? 2 : pieces == 2 ? 1 : 0;
+  const uint64_t grid = ctr_cached_grid(nblocks, tail, shape, &p);
   return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, kTtableSmemEnc, stream,
                     static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, p);
+}
+
+// The TMA-staged variant (timeouts: the device counter of given-up waits).
+template <int NR>
+cudaError_t launch_ctr_bulk(const void* in, void* out, uint64_t nblocks, uint32_t tail, const RoundKeys& rk,
+                            const CtrParams& cp, const LaunchShape& shape, unsigned int* timeouts,
+                            cudaStream_t stream) {
+  auto kern = ttable_ctr_bulk_kernel<NR>;
+  const int smem = bulk_smem_bytes(shape.cta_threads / 32);
+  cudaError_t e = ensure_dynamic_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  CtrParams p = cp;
+  const uint64_t grid = ctr_cached_grid(nblocks, tail, shape, &p);
+  return launch_pdl(kern, static_cast<unsigned>(grid), shape.cta_threads, smem, stream,
+                    static_cast<const uint4*>(in), static_cast<uint4*>(out), nblocks, tail, rk, p, timeouts);
 }
 
 template <Op OP, int NR, int BPT>
