@@ -46,7 +46,8 @@ cudaError_t launch_ctr_bulk(const void* in, void* out, uint64_t nblocks, uint32_
                             cudaStream_t stream) {
   auto kern = ttable_ctr_bulk_kernel<NR>;
   const int smem = bulk_smem_bytes(shape.cta_threads / 32);
-  cudaError_t e = ensure_dynamic_smem(kern, smem);
+  // opt in once to the largest size any CTA shape needs (the opt-in is cached per kernel)
+  cudaError_t e = ensure_dynamic_smem(kern, bulk_smem_bytes(32));
   if (e != cudaSuccess) return e;
   CtrParams p = cp;
   const uint64_t grid = ctr_cached_grid(nblocks, tail, shape, &p);
