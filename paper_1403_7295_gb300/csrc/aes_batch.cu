@@ -80,26 +80,9 @@ constexpr size_t batch_table_bytes() {
   return OPB == kBatchEcbDec ? 192 * 1024 : 128 * 1024;
 }
 
-// The CTA's tile claims, double-buffered: tile i reads entry i & 1 while
-// warp 0 writes tile i + 1 into the other entry.  They sit at the end of the
-// dynamic shared memory: the kernel has no static shared variables, so its
-// tables start at shared address 0 and every lookup address is the PRMT
-// result plus an immediate offset.
-struct TileClaims {
-  unsigned long long tile[2];
-  uint32_t mlo[2], mhi[2];
-  uint32_t span;  // next 256-block span of the current window
-  uint32_t pad[3];
-};
-
-template <int OPB>
-constexpr size_t batch_window_bytes() {
-  return WindowSize<OPB>::value * (kRkStride * 4 + sizeof(Slot));
-}
-
 template <int OPB>
 constexpr size_t batch_smem_bytes() {
-  return batch_table_bytes<OPB>() + batch_window_bytes<OPB>() + sizeof(TileClaims);
+  return batch_table_bytes<OPB>() + WindowSize<OPB>::value * (kRkStride * 4 + sizeof(Slot));
 }
 
 // ---------------------------------------------------------------- scan ----
@@ -1123,12 +1106,11 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
   constexpr int kWin = WindowSize<OPB>::value;
   constexpr bool kDec = OPB == kBatchEcbDec;
   extern __shared__ __align__(16) uint32_t smem[];
-  TileClaims& claims = *reinterpret_cast<TileClaims*>(reinterpret_cast<char*>(smem) + batch_table_bytes<OPB>() +
-                                                      batch_window_bytes<OPB>());
-  unsigned long long* s_tile = claims.tile;
-  uint32_t* s_mlo = claims.mlo;
-  uint32_t* s_mhi = claims.mhi;
-  uint32_t& s_span = claims.span;
+  // the claimed tile, double-buffered: tile i reads entry i & 1 while warp 0
+  // writes tile i + 1 into the other entry
+  __shared__ unsigned long long s_tile[2];
+  __shared__ uint32_t s_mlo[2], s_mhi[2];
+  __shared__ uint32_t s_span;  // next 256-block span of the current window
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.blk_off[a.n];
@@ -1212,8 +1194,7 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
 template <int OPB, bool kRegKeys>
 cudaError_t launch_build(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
   constexpr size_t smem = batch_smem_bytes<OPB>();
-  static_assert(smem <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
-  static_assert(sizeof(TileClaims) % 16 == 0 && batch_window_bytes<OPB>() % 16 == 0, "16-byte aligned regions");
+  static_assert(smem + 64 <= 227 * 1024, "batch kernel shared memory over the 227 KB limit");
   auto kern = batch_kernel<OPB, kRegKeys>;
   cudaError_t e = ensure_dynamic_smem(kern, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
