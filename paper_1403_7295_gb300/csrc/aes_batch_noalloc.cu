@@ -2,12 +2,12 @@
 // the batch pipeline's workspace (per-message block offsets, chunk totals,
 // tile counter) lives in one file-scope device array instead of a caller
 // buffer.  The work itself is the ordinary aes_batch_submit path.
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "aes_batch.h"
+#include "aes_smem_attr.h"
 #include "aesgpu.h"
 
 namespace {
@@ -38,52 +38,13 @@ struct ScratchEntry {
 std::mutex g_mu;
 ScratchEntry g_scratch[kMaxDevices] = {};
 
-// The two driver calls that name the current context, fetched through the
-// runtime (so the library needs no link against the driver library).
-using CtxGetCurrentFn = CUresult (*)(CUcontext*);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
-struct DriverCalls {
-  CtxGetCurrentFn get_current = nullptr;
-  CtxGetIdFn get_id = nullptr;
-  bool ok = false;
-};
-
-const DriverCalls& driver_calls() {
-  static const DriverCalls calls = [] {
-    DriverCalls c;
-    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
-    void* f1 = nullptr;
-    void* f2 = nullptr;
-    // cuCtxGetId exists from CUDA 12.0 on.
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
-        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
-        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2) {
-      c.get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
-      c.get_id = reinterpret_cast<CtxGetIdFn>(f2);
-      c.ok = true;
-    }
-    return c;
-  }();
-  return calls;
-}
-
-// ID of the calling thread's current context, 0 if there is none yet.
-bool current_context_id(unsigned long long* id) {
-  const DriverCalls& d = driver_calls();
-  if (!d.ok) return false;
-  CUcontext ctx = nullptr;
-  if (d.get_current(&ctx) != CUDA_SUCCESS) return false;
-  *id = 0;
-  return ctx == nullptr || d.get_id(ctx, id) == CUDA_SUCCESS;
-}
-
 aes_status scratch_for_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
   if (dev < 0 || dev >= kMaxDevices) return AES_ERR_ARG;
   unsigned long long id = 0;
-  if (!current_context_id(&id)) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
+  if (!aesgpu::current_context_id(&id)) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
   std::lock_guard<std::mutex> lock(g_mu);
   ScratchEntry& entry = g_scratch[dev];
   if (id == 0 || entry.ptr == nullptr || entry.ctx_id != id) {
@@ -93,7 +54,7 @@ aes_status scratch_for_current_device(void** out) {
     // Binds (or creates) the device's primary context when none is current.
     e = cudaGetSymbolAddress(&p, g_batch_scratch);
     if (e != cudaSuccess) return aesgpu::record_cuda_failure(e);
-    if (!current_context_id(&id) || id == 0) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
+    if (!aesgpu::current_context_id(&id) || id == 0) return aesgpu::record_cuda_failure(cudaErrorNotSupported);
     entry = ScratchEntry{id, p};
   }
   *out = entry.ptr;

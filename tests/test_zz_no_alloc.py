@@ -6,10 +6,10 @@ stall other streams, or inside a framework that owns every device
 allocation.  ``aes_batch_submit_noalloc`` serves them by keeping the batch
 workspace in a fixed device array of the library.  These tests call it
 through the C ABI for two different batches in a row (then the first one
-again, over the array the second left behind), and for a batch of exactly
-the message cap twice, and compare every output byte, status and output
-length with the workspace-taking ``aes_batch_submit`` (AES is exact, so the
-tolerance is zero), and check the size limit.
+again, over the array the second left behind), for a batch of exactly the
+message cap twice, and across CUDA contexts, and compare every output byte,
+status and output length with the workspace-taking ``aes_batch_submit`` (AES
+is exact, so the tolerance is zero), and check the size limit.
 
 This file sorts last so a run that stops at the first failure has already run
 everything else; it also passes on its own in a fresh process.
@@ -119,6 +119,20 @@ def test_noalloc_at_the_message_cap(torch, lib):
         for g, r in zip(snapshot(b), ref):
             assert torch.equal(g, r)
     assert int((b.status != 0).sum()) == 0
+
+
+def test_noalloc_follows_the_current_context(torch):
+    """The scratch address is kept per CUDA context: in a child process (driver
+    API only) the call runs in the device's primary context, in a second
+    context made with cuCtxCreate, and in the primary one again, each time
+    equal to aes_batch_submit byte for byte (tests/noalloc_context_child.py)."""
+    import os
+    import subprocess
+    import sys
+
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "noalloc_context_child.py")
+    r = subprocess.run([sys.executable, child], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("OK"), (r.returncode, r.stdout[-2000:], r.stderr[-2000:])
 
 
 def test_noalloc_size_limit_and_arguments(torch, lib):
