@@ -417,7 +417,7 @@ def roofline(args, bits, nbytes, per_launch_s, probes, sms, clock_mhz, hbm_peak,
     lk = read_profile_field(args, "lookups_per_block_measured:")
     lk_src = "ncu (committed summary of this kernel source)"
     if lk is None:
-        lk = executed_lookups_per_block(args, bits, nbytes)
+        lk = executed_lookups_per_block(args, bits, nbytes, sms)
         lk_src = "the kernel's own lookup count, derived from its structure (no current ncu summary)"
     alu = read_profile_field(args, "alu_instructions_per_block_measured:")
     rl.update({"bound": "alu", "unit": "Glookup/s", "achieved": None, "peak": None, "frac": None,
@@ -454,7 +454,7 @@ def roofline(args, bits, nbytes, per_launch_s, probes, sms, clock_mhz, hbm_peak,
     return rl
 
 
-def executed_lookups_per_block(args, bits, nbytes):
+def executed_lookups_per_block(args, bits, nbytes, sms):
     """Table lookups the default CTR kernel executes per block, from its
     structure: 16 per full round from round 3 on and in the final round, 5
     for rounds 1-2 (the counter byte's round-1 lookup and its four round-2
@@ -465,7 +465,7 @@ def executed_lookups_per_block(args, bits, nbytes):
         return 16 * nr
     units = nbytes // 16 + (1 if nbytes % 16 else 0)
     runs = (units + 255) // 256
-    warps = 152 * 32
+    warps = sms * 32  # one 1024-thread CTA per SM
     whole = runs - runs % warps
     tail = runs - whole
     pieces = whole + tail * (8 if tail and warps // tail >= 8 else 4 if tail and warps // tail >= 4
