@@ -63,8 +63,7 @@ def test_three_ceilings_and_the_binding_term():
     if "alu" in terms:  # the committed summary matches the kernel: the INT32 term is there
         alu = rl["int32"]["alu_instructions_per_block"]
         assert terms["alu"] == pytest.approx(64 * SMS * CLOCK_MHZ * 1e6 / alu * 16 / 1e9, rel=1e-3)
-        assert rl["int32"]["frac"] == pytest.approx(value * 1e9 / 16 * alu / (64 * SMS * CLOCK_MHZ * 1e6) / 1e9,
-                                                    rel=1e-3)
+        assert rl["int32"]["frac"] == pytest.approx(value * 1e9 / 16 * alu / (64 * SMS * CLOCK_MHZ * 1e6), rel=1e-3)
 
 
 def test_a_stale_summary_is_not_used(monkeypatch, tmp_path):
