@@ -257,10 +257,12 @@ __device__ __forceinline__ void expand_key_nk(const Tabs& T, const char* sb, uin
                                               const uint8_t* key, uint32_t* rk) {
   constexpr int kWords = 4 * (NK + 7);
   uint32_t w[NK];
+  uint32_t q[4];  // the round key being assembled: written as one 128-bit store (rk is 16-byte aligned)
 #pragma unroll
   for (int i = 0; i < NK; ++i) {
     w[i] = load_le32(key + 4 * i);
-    rk[i] = w[i];
+    q[i & 3] = w[i];
+    if ((i & 3) == 3) *reinterpret_cast<uint4*>(rk + i - 3) = make_uint4(q[0], q[1], q[2], q[3]);
   }
   uint32_t rcon = 1;
 #pragma unroll
@@ -273,7 +275,8 @@ __device__ __forceinline__ void expand_key_nk(const Tabs& T, const char* sb, uin
       t = sub_word(T, sb, sb_off, t);
     }
     w[i % NK] ^= t;  // w[i] = w[i - NK] ^ t
-    rk[i] = w[i % NK];
+    q[i & 3] = w[i % NK];
+    if ((i & 3) == 3) *reinterpret_cast<uint4*>(rk + i - 3) = make_uint4(q[0], q[1], q[2], q[3]);
   }
 }
 
@@ -1032,28 +1035,27 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       if (OPB == kBatchCtr) {
         const uint4 ivw = *reinterpret_cast<const uint4*>(a.iv + 16ull * m);
         r.ctr0 = __byte_perm(ivw.w, 0, 0x0123) - b0;
-        const uint32_t s0 = ivw.x ^ rk[0], s1 = ivw.y ^ rk[1], s2 = ivw.z ^ rk[2];
-        rk[kCtrRk0w3] = rk[3];
+        const uint4 k0 = lds128(rk), k1 = lds128(rk + 4), k2 = lds128(rk + 8);
+        const uint32_t s0 = ivw.x ^ k0.x, s1 = ivw.y ^ k0.y, s2 = ivw.z ^ k0.z;
         // round-1 columns without the counter column's lookups (column 3 of the state)
-        rk[kCtrC1 + 0] = rk[4] ^ T.t0(s0) ^ T.t1(s1) ^ T.t2(s2);
-        rk[kCtrC1 + 1] = rk[5] ^ T.t0(s1) ^ T.t1(s2) ^ T.t3(s0);
-        rk[kCtrC1 + 2] = rk[6] ^ T.t0(s2) ^ T.t2(s0) ^ T.t3(s1);
-        rk[kCtrC1 + 3] = rk[7] ^ T.t1(s0) ^ T.t2(s1) ^ T.t3(s2);
+        const uint32_t c1x = k1.x ^ T.t0(s0) ^ T.t1(s1) ^ T.t2(s2);
+        const uint32_t c1y0 = k1.y ^ T.t0(s1) ^ T.t1(s2) ^ T.t3(s0);
+        const uint32_t c1z0 = k1.z ^ T.t0(s2) ^ T.t2(s0) ^ T.t3(s1);
+        const uint32_t c1w0 = k1.w ^ T.t1(s0) ^ T.t2(s1) ^ T.t3(s2);
         // the counter run holding most of the message's blocks (a message of
         // < 512 blocks spans at most three runs): its round-1/2 constants
         const uint32_t c_first = r.ctr0 + b0;
         const uint32_t in_first = 256 - (c_first & 255u);
         const uint32_t run = (c_first >> 8) + (nb > 2 * in_first ? 1 : 0);
-        const uint32_t xr = __byte_perm(run << 8, 0, 0x0123) ^ rk[3];
-        const uint32_t c1y = rk[kCtrC1 + 1] ^ T.t2(xr), c1z = rk[kCtrC1 + 2] ^ T.t1(xr),
-                       c1w = rk[kCtrC1 + 3] ^ T.t0(xr);
-        rk[kRunWords + 1] = run;
-        rk[kRunWords + 2] = xr;
-        rk[kRunWords + 3] = rk[kCtrC1 + 0];
-        rk[kRunD + 0] = rk[8] ^ T.t1(c1y) ^ T.t2(c1z) ^ T.t3(c1w);
-        rk[kRunD + 1] = rk[9] ^ T.t0(c1y) ^ T.t1(c1z) ^ T.t2(c1w);
-        rk[kRunD + 2] = rk[10] ^ T.t0(c1z) ^ T.t1(c1w) ^ T.t3(c1y);
-        rk[kRunD + 3] = rk[11] ^ T.t0(c1w) ^ T.t2(c1y) ^ T.t3(c1z);
+        const uint32_t xr = __byte_perm(run << 8, 0, 0x0123) ^ k0.w;
+        const uint32_t c1y = c1y0 ^ T.t2(xr), c1z = c1z0 ^ T.t1(xr), c1w = c1w0 ^ T.t0(xr);
+        // words 60..71 of the slot, three 128-bit stores: c1, then (rk0 word 3,
+        // run, xr, c1 column 0), then the run's round-2 columns
+        *reinterpret_cast<uint4*>(rk + kCtrC1) = make_uint4(c1x, c1y0, c1z0, c1w0);
+        *reinterpret_cast<uint4*>(rk + kRunWords) = make_uint4(k0.w, run, xr, c1x);
+        *reinterpret_cast<uint4*>(rk + kRunD) =
+            make_uint4(k2.x ^ T.t1(c1y) ^ T.t2(c1z) ^ T.t3(c1w), k2.y ^ T.t0(c1y) ^ T.t1(c1z) ^ T.t2(c1w),
+                       k2.z ^ T.t0(c1z) ^ T.t1(c1w) ^ T.t3(c1y), k2.w ^ T.t0(c1w) ^ T.t2(c1y) ^ T.t3(c1z));
       }
       r.info = nr | static_cast<uint32_t>(len & 15u) << 8 | lane << 16;
       r.full_end = b0 + static_cast<uint32_t>(len / 16);
