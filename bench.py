@@ -468,8 +468,11 @@ def executed_lookups_per_block(args, bits, nbytes, sms):
     warps = sms * 32  # one 1024-thread CTA per SM
     whole = runs - runs % warps
     tail = runs - whole
-    pieces = whole + tail * (8 if tail and warps // tail >= 8 else 4 if tail and warps // tail >= 4
-                             else 2 if tail and warps // tail >= 2 else 1)
+    # the kernel's split of the last partial wave: P pieces of 8 / P steps per run,
+    # P minimising the busiest warp's cost there in quarter steps (4 per step, 1 per
+    # piece's setup), the fewest pieces on a tie
+    split = min((1, 2, 4, 8), key=lambda p: (-(-tail * p // warps) * (32 // p + 1), p)) if tail else 1
+    pieces = whole + tail * split
     return round(16 * (nr - 2) + 5 + 15 * pieces / (nbytes / 16), 3)
 
 

@@ -232,13 +232,27 @@ __global__ void __launch_bounds__(1024, 1)
 //
 // Runs that fill whole waves of the grid's warps go one per warp.  The runs
 // of the last, partial wave are split into ctr_tail_pieces() pieces of 8/P
-// steps each, so that every warp has work there (each piece computes its
-// run's constants).  The launch computes the split for its grid
-// (CtrParams::whole_runs, tail_shift).
+// steps each.  A piece costs its steps plus its own setup: the run's
+// constants (15 lookups) and a loop that is not unrolled, about a quarter
+// step together.  P is chosen so the busiest warp's share of that wave costs
+// least, the fewest pieces on a tie: ceil(runs * P / warps) pieces of
+// 4 * 8 / P + 1 quarter steps.  (At 64 MiB, 1,792 tail runs over 4,864
+// warps: three one-step pieces, 15 quarter steps, against one four-step
+// piece, 17.  At 16 MiB the 4,096 runs stay whole, one per warp of a
+// 128-CTA grid: 33 against 35 for seven one-step pieces.)  The launch
+// computes the split for its grid (CtrParams::whole_runs, tail_shift).
 __host__ __device__ __forceinline__ uint32_t ctr_tail_pieces(uint64_t tail_runs, uint64_t warps) {
-  if (tail_runs == 0) return 1;
-  const uint64_t q = warps / tail_runs;
-  return q >= 8 ? 8 : q >= 4 ? 4 : q >= 2 ? 2 : 1;
+  if (tail_runs == 0 || warps == 0) return 1;
+  uint32_t best = 1;
+  uint64_t best_cost = ~0ull;
+  for (uint32_t p = 1; p <= 8; p *= 2) {
+    const uint64_t cost = (tail_runs * p + warps - 1) / warps * (32 / p + 1);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = p;
+    }
+  }
+  return best;
 }
 
 // Steps [k0, k1) of one run.  kWhole: the whole run (k0 = 0, k1 = 8, known

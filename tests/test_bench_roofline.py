@@ -26,14 +26,18 @@ def args(**kw):
 def test_structural_lookup_count():
     """16 lookups per round from round 3 plus the final round, 5 for rounds
     1-2, and 15 per counter-run piece (one piece per run in whole waves, the
-    last partial wave's runs split in 2, 4 or 8)."""
+    last partial wave's runs split in 1, 2, 4 or 8 pieces so the busiest warp
+    has the least to do there, each piece's setup counted as a quarter step)."""
     a = args()
     nbytes = 8 << 30
     runs = nbytes // 16 // 256
     warps = SMS * 32
     whole = runs - runs % warps
     tail = runs - whole
-    pieces = whole + tail * (8 if warps // tail >= 8 else 4 if warps // tail >= 4 else 2 if warps // tail >= 2 else 1)
+    # busiest warp's cost in quarter steps: 4 per step, 1 for each piece's setup
+    busiest = {p: -(-tail * p // warps) * (4 * (8 // p) + 1) for p in (1, 2, 4, 8)}
+    split = min(p for p in busiest if busiest[p] == min(busiest.values()))
+    pieces = whole + tail * split
     want = 16 * 8 + 5 + 15 * pieces / (nbytes / 16)
     assert bench.executed_lookups_per_block(a, 128, nbytes, SMS) == pytest.approx(want, abs=1e-3)
     assert bench.executed_lookups_per_block(a, 256, nbytes, SMS) == pytest.approx(want + 64, abs=1e-3)
