@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(1024, 1)
 // warps: three one-step pieces, 15 quarter steps, against one four-step
 // piece, 17.  At 16 MiB the 4,096 runs stay whole, one per warp of a
 // 128-CTA grid: 33 against 35 for seven one-step pieces.)  The launch
-// computes the split for its grid (CtrParams::whole_runs, tail_shift).
+// computes the split for its grid (CtrParams::whole_runs, tail_shift); a
+// last wave left whole (P = 1) joins the full waves' loop.
 __host__ __device__ __forceinline__ uint32_t ctr_tail_pieces(uint64_t tail_runs, uint64_t warps) {
   if (tail_runs == 0 || warps == 0) return 1;
   uint32_t best = 1;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(1024, 1)
   const uint64_t runs = (units + off0 + 255) / 256;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
   const uint64_t wid = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const uint64_t whole = cp.whole_runs;  // runs in full waves (runs - runs mod warps)
+  const uint64_t whole = cp.whole_runs;  // runs one per warp: the full waves, and a last wave left unsplit
   for (uint64_t run = wid; run < whole; run += warps)
     ctr_run_steps<NR, true>(T, in, out, nblocks, units, tail_bytes, rk, cp, off0, run, 0, 8, lane);
   const uint32_t shift = cp.tail_shift, steps = 8u >> shift;

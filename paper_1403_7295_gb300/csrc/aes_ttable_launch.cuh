@@ -20,8 +20,9 @@ inline uint64_t ctr_cached_grid(uint64_t nblocks, uint32_t tail, const LaunchSha
   const uint64_t needed = (work + warps_per_cta - 1) / warps_per_cta;
   if (grid > needed) grid = needed > 0 ? needed : 1;
   const uint64_t warps = grid * warps_per_cta;
-  p->whole_runs = runs - runs % warps;
-  const uint32_t pieces = ctr_tail_pieces(runs - p->whole_runs, warps);
+  const uint32_t pieces = ctr_tail_pieces(runs % warps, warps);
+  // a last wave left unsplit runs through the (unrolled) loop of the whole waves
+  p->whole_runs = pieces == 1 ? runs : runs - runs % warps;
   p->tail_shift = pieces == 8 ? 3 : pieces == 4 ? 2 : pieces == 2 ? 1 : 0;
   return grid;
 }

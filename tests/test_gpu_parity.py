@@ -180,6 +180,28 @@ def test_whole_buffer_64MiB(A, torch, oracle, bits, op):
     assert g.intact()
 
 
+@pytest.mark.parametrize("mib,bits", [(2, 128), (4, 256), (16, 256), (32, 128), (48, 256), (128, 128),
+                                      (256, 256)])
+def test_ctr_every_tail_split_whole_buffer(A, torch, oracle, mib, bits):
+    """The default CTR kernel splits the runs of its last, partial wave into
+    1, 2, 4 or 8 pieces, chosen from the run count and the grid: with 4,864
+    warps, 2 MiB takes 8 pieces and 4 MiB 4 on a shrunk grid, 16 MiB keeps
+    its 4,096 runs whole on 128 CTAs, and after whole waves 32 and 128 MiB
+    take 4 pieces, 48 MiB 8 and 256 MiB 2.  Every byte against the threaded
+    oracle, with a counter start inside a run and a ragged last block."""
+    n = (mib << 20) + 11
+    seed = 70 + mib
+    key = synth.key_bytes(seed, bits)
+    iv = synth.iv_bytes(seed, counter0=0x0001F0C5)
+    x = synth.bytes_np(seed, synth.STREAM_DATA, n)
+    ks = A.aes_expand_key(key)
+    g = Guarded(n)
+    A.aes_ctr_xcrypt(ks, iv, to_dev(x), g.view)
+    torch.cuda.synchronize()
+    assert np.array_equal(g.numpy(), oracle.ctr_xcrypt(key, bits, iv, x, nthreads=host_threads()))
+    assert g.intact()
+
+
 @pytest.mark.parametrize("bits,op", [(128, "ctr"), (256, "ctr"), (128, "ecb_enc"), (128, "ecb_dec")])
 def test_whole_buffer_1GiB(A, torch, oracle, bits, op):
     """1 GiB at the bench's launch shape, every byte against the threaded
