@@ -69,6 +69,8 @@ def parse_args():
                    help="'batched': time only the batched varlen workload; 'small': only the "
                         "1,000,000 packet-sized messages (profiling entries)")
     p.add_argument("--batch-msgs", type=int, default=16384, help="messages in the batched varlen workload")
+    p.add_argument("--short-path", choices=["auto", "groups", "lanes"], default="auto",
+                   help="with --only: the batch's short-message path (aes_batch_config.short_path)")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="duration of the serving leg (Poisson 50k req/s, the configured 60 s); 0 skips it "
                         "and the loaded point")
@@ -628,12 +630,19 @@ def batched_only(args):
     in_off, total = B.pack_offsets(lengths)
     data = synth.bytes_torch(3, synth.STREAM_DATA, total, device="cuda")
     b = B.Batch(B.BATCH_CTR, data, in_off, lengths, keys=wl["keys"], key_bits=wl["key_bits"], ivs=wl["ivs"])
-    b.capture(B.AesBatchConfig(args.cta or 1024, 8192 if small else 32768, 0, 0))
+    path = {"auto": B.SHORT_AUTO, "groups": B.SHORT_GROUPS, "lanes": B.SHORT_LANES}[args.short_path]
+    b.capture(B.AesBatchConfig(args.cta or 1024, 8192 if small else 32768, 0, path))
     ms = time_graph(torch, b, args.steps) if args.warmup >= 3 else time_device(torch, b.replay, args.steps, args.warmup)
     gbps = b.total_input_bytes() * args.steps / (ms / 1e3) / 1e9
     name = "1,000,000 packet-sized messages" if small else f"{args.batch_msgs} messages"
     print(json.dumps({"workload": f"batched varlen CTR, {name}", "bytes": b.total_input_bytes(),
+                      "short_path": args.short_path,
                       "gbps": round(gbps, 1), "ms_per_batch": round(ms / args.steps, 3)}), flush=True)
+
+
+# aes_batch_config.short_path values, as reported in the batched results
+SHORT_PATH_NAMES = {0: "auto", 1: "groups (per-warp message groups, keys in shared memory)",
+                    2: "lanes (one lane per message, keys in registers)"}
 
 
 def batched_arm(torch, A):
@@ -641,7 +650,9 @@ def batched_arm(torch, A):
     key sizes, CTR, one persistent launch in a CUDA graph with an autotuned
     shape, against the byte-weighted harmonic mix of single-buffer 1 GiB CTR
     rates; (b) 1,000,000 packet-sized AES-128 CTR messages with keys expanded
-    on the device vs pre-expanded schedules."""
+    on the device vs pre-expanded schedules.  The autotuner picks the launch
+    shape and, for CTR, the short-message path (per-warp groups or one lane
+    per message) by timing both on the batch itself."""
     from paper_1403_7295_gb300 import batch as B
     from synth import workloads as W
 
@@ -678,8 +689,9 @@ def batched_arm(torch, A):
         "per_batch": {k: st[k] for k in ("median_ms", "p99_ms", "paper_mean_ms")},
         "plain_ctr_1GiB_gbps": {str(k): round(v, 1) for k, v in rates.items()},
         "plain_mix_gbps": round(mix, 1), "ratio_vs_plain": round(gbps / mix, 4),
-        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
-        "kernels_per_batch": 4, "graph": True,
+        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks,
+                   "short_path": SHORT_PATH_NAMES[cfg.short_path]},
+        "kernels_per_batch": 4 if cfg.short_path != B.SHORT_LANES else 6, "graph": True,
     }
     # the same messages as ECB + PKCS#7, encrypt then decrypt, against the ECB mix
     ecb_rates = {}
@@ -732,7 +744,8 @@ def batched_arm(torch, A):
     sched = torch.frombuffer(table, dtype=torch.uint8).cuda()
     b2 = B.Batch(B.BATCH_CTR, data, in_off, lengths, schedules=sched, n_schedules=b.n,
                  sched_idx=np.arange(b.n, dtype=np.uint32), ivs=wl["ivs"], out=b.out)
-    b2.capture(cfg)
+    cfg2 = B.autotune(b2)  # its own choice: resident schedules load differently
+    b2.capture(cfg2)
     ms_pre = time_graph(torch, b2, steps)
     g_dev = nbytes * steps / (ms_dev / 1e3) / 1e9
     out["small_1M"] = {
@@ -743,7 +756,11 @@ def batched_arm(torch, A):
         "bytes": nbytes, "ms_per_batch_device_keys": round(ms_dev / steps, 3),
         "ms_per_batch_preexpanded": round(ms_pre / steps, 3),
         "per_batch_device_keys": {k: st_small[k] for k in ("median_ms", "p99_ms", "paper_mean_ms")},
-        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks},
+        "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks,
+                   "short_path": SHORT_PATH_NAMES[cfg.short_path]},
+        "kernels_per_batch": 4 if cfg.short_path != B.SHORT_LANES else 6,
+        "launch_preexpanded": {"cta_threads": cfg2.cta_threads, "tile_blocks": cfg2.tile_blocks,
+                               "short_path": SHORT_PATH_NAMES[cfg2.short_path]},
     }
     return out
 

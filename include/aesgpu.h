@@ -220,6 +220,19 @@ typedef struct aes_batch {
     int32_t *status;              /* [n_msgs] out: aes_status per message (may be NULL) */
 } aes_batch;
 
+/* aes_batch_config.short_path: how the messages of fewer than 512 blocks run. */
+#define AES_BATCH_SHORT_AUTO 0   /* the library's measured choice: LANES for CTR batches of 262,144
+                                    messages or more, GROUPS otherwise */
+#define AES_BATCH_SHORT_GROUPS 1 /* every op: each warp of the persistent kernel takes groups of
+                                    consecutive messages, their round keys in shared memory */
+#define AES_BATCH_SHORT_LANES 2  /* CTR only: one lane per message of fewer than 128 blocks, its
+                                    round keys in registers; those messages are first sorted by key
+                                    size and length (a memset and one more launch), then a kernel of
+                                    their own runs them after the persistent kernel, which keeps the
+                                    longer short messages (other ops: AES_ERR_ARG).  Faster on large
+                                    batches of packet-sized messages, slower on small batches: a lane
+                                    walks its message's blocks one after another */
+
 /* Optional launch shape of the persistent kernel; zero fields = default. */
 typedef struct aes_batch_config {
     int32_t cta_threads;  /* 256..1024, multiple of 32; up to 512 selects the build with 128
@@ -228,16 +241,18 @@ typedef struct aes_batch_config {
     int32_t tile_blocks;  /* 16-byte blocks a CTA claims at a time: multiple of cta_threads, <= 2^20;
                              0 = sized from the batch: ~4 tiles per CTA of the long messages' blocks,
                              at most 65536 */
-    int32_t grid_ctas;    /* 0 = one per SM */
-    int32_t reserved;
+    int32_t grid_ctas;    /* 0 = one per SM (also the lane kernel's grid) */
+    int32_t short_path;   /* AES_BATCH_SHORT_* */
 } aes_batch_config;
 
 /* Bytes of device workspace aes_batch_submit needs for n_msgs messages. */
 size_t aes_batch_workspace_size(uint32_t n_msgs);
 
 /* Enqueue one batch on `stream` (4 kernel launches: count+scan, chunk scan,
- * offset fix, persistent cipher kernel; no allocation, no host sync, so the
- * call can be captured into a CUDA graph and replayed).  d_workspace: device,
+ * offset fix, persistent cipher kernel; on the lane path of short CTR
+ * messages also a memset of the bin counts, the scatter into bin order and
+ * the lane kernel; no allocation, no host sync, so the call can be captured
+ * into a CUDA graph and replayed).  d_workspace: device,
  * 256-byte aligned, at least aes_batch_workspace_size(n_msgs) bytes; its
  * contents need no initialisation.  Per-message failures (bad key size,
  * unaligned offset, bad ECB length or padding) are reported in status[m]
@@ -258,7 +273,7 @@ aes_status aes_batch_submit_ex(const aes_batch *b, void *d_workspace, size_t wor
  * paper has no counterpart; this is a deployment convenience.
  *
  * The workspace is one file-scope device array of the library, sized for
- * AES_BATCH_NOALLOC_MAX_MSGS messages (about 513 KiB); every GPU that loads
+ * AES_BATCH_NOALLOC_MAX_MSGS messages (about 909 KiB); every GPU that loads
  * libaesgpu.so holds it until the process exits.  The call allocates nothing
  * and calls no allocating routine; inputs and outputs are the caller's as in
  * aes_batch_submit, with the same rules and per-message status.
@@ -457,9 +472,9 @@ aes_status aes_server_replay(aes_server *s, uint64_t n, const double *arrival_s,
                              const uint64_t *capture_off);
 
 /* Device waits that gave up: the TMA-staged CTR variant (AES_VARIANT_TTABLE_BULK)
- * bounds each wait for its staged copy to about a second of SM clock; a warp
- * whose copy has not landed by then counts one timeout, leaves its remaining
- * blocks unwritten and stops.  *count gets the timeouts counted on the current
+ * and the batch's lane kernel (AES_BATCH_SHORT_LANES) bound each wait for a
+ * staged copy to about a second of SM clock; a warp whose copy has not landed
+ * by then counts one timeout, leaves its remaining blocks unwritten and stops.  *count gets the timeouts counted on the current
  * device since the last call, and the count restarts at 0.  Synchronous (it
  * reads a device word): call it once the work it covers has completed.
  * Returns AES_OK, AES_ERR_TIMEOUT when *count > 0, AES_ERR_ARG for a null

@@ -190,8 +190,9 @@ def aes_ctr_iv_advance(iv, first_block: int) -> bytes:
 
 
 def aes_take_wait_timeouts() -> int:
-    """Bounded device waits (of the TMA-staged CTR variant) that gave up on
-    the current device since the last call; the count restarts at 0."""
+    """Bounded device waits (of the TMA-staged CTR variant and the batch's
+    lane kernel) that gave up on the current device since the last call; the
+    count restarts at 0."""
     n = ctypes.c_uint32(0)
     rc = lib().aes_take_wait_timeouts(ctypes.byref(n))
     if rc not in (AES_OK, 9):  # 9: AES_ERR_TIMEOUT, reported through the count

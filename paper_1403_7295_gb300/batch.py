@@ -37,10 +37,13 @@ class AesBatch(ctypes.Structure):
     ]
 
 
+SHORT_AUTO, SHORT_GROUPS, SHORT_LANES = 0, 1, 2  # AES_BATCH_SHORT_*
+
+
 class AesBatchConfig(ctypes.Structure):
     """Mirror of ``aes_batch_config``; zero fields mean "library default"."""
     _fields_ = [("cta_threads", ctypes.c_int32), ("tile_blocks", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("short_path", ctypes.c_int32)]
 
 
 def _declare():
@@ -219,12 +222,15 @@ def _bucket(batch: Batch) -> str:
     name = torch.cuda.get_device_name()
     n = batch.n
     mean = batch.total_input_bytes() / max(1, n)
-    return f"{name}|op{batch.op}|n2^{int(np.log2(max(n, 1)))}|mean2^{int(np.log2(max(mean, 1)))}"
+    keys = "keys" if batch.keys is not None else "schedules"  # device expansion or resident schedules
+    return f"{name}|op{batch.op}|{keys}|n2^{int(np.log2(max(n, 1)))}|mean2^{int(np.log2(max(mean, 1)))}"
 
 
 def autotune(batch: Batch, reps: int = 3, use_cache: bool = True) -> AesBatchConfig:
-    """Pick (cta_threads, tile_blocks) for this batch shape by CUDA-event timing;
-    the choice is cached per (GPU, op, message-count and mean-size bucket)."""
+    """Pick (cta_threads, tile_blocks, short_path) for this batch shape by
+    CUDA-event timing (the short-message path only for CTR, the one op with
+    two); the choice is cached per (GPU, op, message-count and mean-size
+    bucket)."""
     import torch
 
     key = _bucket(batch)
@@ -234,12 +240,13 @@ def autotune(batch: Batch, reps: int = 3, use_cache: bool = True) -> AesBatchCon
             cache = json.load(open(_CACHE_PATH))
         except (OSError, ValueError):
             cache = {}
-    if use_cache and key in cache:
-        cta, tile = cache[key]
-        return AesBatchConfig(cta, tile, 0, 0)
+    if use_cache and key in cache and len(cache[key]) == 3:
+        cta, tile, path = cache[key]
+        return AesBatchConfig(cta, tile, 0, path)
+    paths = (SHORT_GROUPS, SHORT_LANES) if batch.op == BATCH_CTR else (SHORT_AUTO,)
     best, best_t = None, float("inf")
-    for cta, tile in CANDIDATES:
-        cfg = AesBatchConfig(cta, tile, 0, 0)
+    for (cta, tile), path in [(c, p) for c in CANDIDATES for p in paths]:
+        cfg = AesBatchConfig(cta, tile, 0, path)
         batch.submit(config=cfg)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -250,7 +257,7 @@ def autotune(batch: Batch, reps: int = 3, use_cache: bool = True) -> AesBatchCon
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1)
         if t < best_t:
-            best, best_t = (cta, tile), t
+            best, best_t = (cta, tile, path), t
     cache[key] = list(best)
     try:
         os.makedirs(os.path.dirname(_CACHE_PATH), exist_ok=True)
@@ -259,4 +266,4 @@ def autotune(batch: Batch, reps: int = 3, use_cache: bool = True) -> AesBatchCon
         os.replace(tmp, _CACHE_PATH)
     except OSError:
         pass
-    return AesBatchConfig(best[0], best[1], 0, 0)
+    return AesBatchConfig(best[0], best[1], 0, best[2])

@@ -328,9 +328,18 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
   int cta = (cfg && cfg->cta_threads) ? cfg->cta_threads : 1024;
   int tile = (cfg && cfg->tile_blocks) ? cfg->tile_blocks : 0;  // 0: sized by the kernel
   int grid = (cfg && cfg->grid_ctas) ? cfg->grid_ctas : sm_count();
+  const int short_path = cfg ? cfg->short_path : AES_BATCH_SHORT_AUTO;
   if (cta < 256 || cta > 1024 || cta % 32) return AES_ERR_ARG;
   if (tile != 0 && (tile < cta || tile > (1 << 20) || tile % cta)) return AES_ERR_ARG;
   if (grid < 1) return AES_ERR_ARG;
+  if (short_path < AES_BATCH_SHORT_AUTO || short_path > AES_BATCH_SHORT_LANES) return AES_ERR_ARG;
+  if (short_path == AES_BATCH_SHORT_LANES && b->op != AES_BATCH_CTR) return AES_ERR_ARG;
+  // The lane path needs enough short messages to keep every warp busy for
+  // several chunks: on packet-sized CTR batches it ran slower than the
+  // per-warp groups at 131,072 messages and faster from 262,144 on.
+  constexpr uint32_t kLaneAutoMsgs = 1u << 18;
+  const bool lanes = short_path == AES_BATCH_SHORT_LANES ||
+                     (short_path == AES_BATCH_SHORT_AUTO && b->op == AES_BATCH_CTR && b->n_msgs >= kLaneAutoMsgs);
   const void* din = nullptr;
   void* dout = nullptr;
   aes_status st = device_view(b->in, &din, false);
@@ -357,7 +366,7 @@ aes_status batch_submit(const aes_batch* b, void* ws, size_t ws_bytes, void* str
   a.iv = b->iv;
   a.out_len = b->out_len;
   a.status = b->status;
-  batch_bind_workspace(&a, ws);
+  batch_bind_workspace(&a, ws, lanes);
   const cudaError_t e = launch_batch(a, cta, grid, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_failure(e);
   return AES_OK;
@@ -499,11 +508,13 @@ aes_status aes_batch_submit(const aes_batch* b, void* d_workspace, size_t worksp
 
 aes_status aes_take_wait_timeouts(uint32_t* count) {
   if (count == nullptr) return AES_ERR_ARG;
-  unsigned int v = 0;
-  const cudaError_t e = take_bulk_timeouts(&v);
+  unsigned int v = 0, w = 0;
+  cudaError_t e = take_bulk_timeouts(&v);
   if (e != cudaSuccess) return cuda_failure(e);
-  *count = v;
-  return v ? AES_ERR_TIMEOUT : AES_OK;
+  e = take_lane_timeouts(&w);
+  if (e != cudaSuccess) return cuda_failure(e);
+  *count = v + w;
+  return v + w ? AES_ERR_TIMEOUT : AES_OK;
 }
 
 int aes_last_cuda_error(void) { return g_last_cuda_error; }

@@ -126,15 +126,46 @@ __device__ __forceinline__ uint64_t message_blocks(const BatchArgs& a, uint32_t 
   return nb;
 }
 
+// Rounds of message m's key (valid once message_blocks accepted it).
+__device__ __forceinline__ uint32_t message_rounds(const BatchArgs& a, uint32_t m) {
+  return a.keys != nullptr ? a.key_bits[m] / 32 + 6 : a.schedules[a.sched_idx[m]].nr;
+}
+
+// Bin of a short CTR message on the lane path: its key-size class, then
+// longest first.
+__device__ __forceinline__ uint32_t lane_bin_of(uint32_t nr, uint64_t nb) {
+  return (nr - 10) / 2 * 512 + (511 - static_cast<uint32_t>(nb));
+}
+
 // Count-kernel step for message m: write its status and output length and
 // return its size in the long-message block space (0 for short messages).
-__device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m) {
+// On the lane path (lane_hist: the CTA's bin counts in shared memory, then
+// its count of short messages left to the per-warp groups) a message of
+// fewer than kLaneMax blocks also gets its bin, counted in lane_hist.
+__device__ __forceinline__ uint64_t count_blocks(const BatchArgs& a, uint32_t m, uint32_t* lane_hist) {
   int32_t st;
   uint64_t olen;
   const uint64_t nb = message_blocks(a, m, &st, &olen);
   if (a.status) a.status[m] = st;
   if (a.out_len) a.out_len[m] = olen;
+  if (lane_hist != nullptr) {
+    uint16_t bin = kLaneNoBin;
+    if (nb > 0 && nb < kLaneMax) {  // nb > 0: the message was accepted
+      const uint32_t b = lane_bin_of(message_rounds(a, m), nb);
+      atomicAdd(lane_hist + b, 1u);
+      bin = static_cast<uint16_t>(b);
+    } else if (nb >= kLaneMax && nb < kShortMax) {
+      atomicAdd(lane_hist + kLaneBins, 1u);
+    }
+    a.lane_bin[m] = bin;
+  }
   return nb >= kShortMax ? nb : 0;
+}
+
+// On the lane path: whether the persistent kernel's per-warp groups have
+// short messages to run (those of kLaneMax blocks or more).
+__device__ __forceinline__ bool groups_have_work(const BatchArgs& a) {
+  return a.lane_bin == nullptr || a.lane_cursor[kLaneBins] != 0;
 }
 
 // Exclusive scan of one value per thread across the CTA; *total = CTA sum.
@@ -164,25 +195,37 @@ __device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* sh,
   return before + x - v;
 }
 
-#ifndef AES_BATCH_REGKEYS_TU  // the scans run from aes_batch.cu's entry point only
-__global__ void __launch_bounds__(kScanThreads) batch_count_scan(const BatchArgs a) {
+#if !defined(AES_BATCH_REGKEYS_TU) && !defined(AES_BATCH_LANES_TU)  // run from aes_batch.cu's entry point only
+__global__ void __launch_bounds__(kScanThreads, 1) batch_count_scan(const BatchArgs a) {
   __shared__ uint64_t sh[64];
+  __shared__ uint32_t lane_hist[kLaneBins + 1];  // the lane path's bin counts of this CTA's messages, and
+                                                 // its short messages left to the per-warp groups
+  const bool lanes = a.lane_bin != nullptr;
+  if (lanes) {
+    for (uint32_t i = threadIdx.x; i <= kLaneBins; i += blockDim.x) lane_hist[i] = 0;
+    __syncthreads();
+  }
   const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems +
                         static_cast<uint64_t>(threadIdx.x) * kScanItems;
   uint64_t cnt[kScanItems], sum = 0;
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k) {
     const uint64_t m = base + k;
-    cnt[k] = m < a.n ? count_blocks(a, static_cast<uint32_t>(m)) : 0;
+    cnt[k] = m < a.n ? count_blocks(a, static_cast<uint32_t>(m), lanes ? lane_hist : nullptr) : 0;
     sum += cnt[k];
   }
   uint64_t total;
-  uint64_t run = cta_exclusive_scan(sum, sh, &total);
+  uint64_t run = cta_exclusive_scan(sum, sh, &total);  // its barriers also order the bin counts
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k) {
     const uint64_t m = base + k;
     if (m < a.n) a.blk_off[m] = run;
     run += cnt[k];
+  }
+  if (lanes) {
+    for (uint32_t i = threadIdx.x; i < kLaneBins; i += blockDim.x)
+      if (lane_hist[i] != 0) atomicAdd(a.lane_hist + i, lane_hist[i]);
+    if (threadIdx.x == 0 && lane_hist[kLaneBins] != 0) atomicAdd(a.lane_cursor + kLaneBins, lane_hist[kLaneBins]);
   }
   if (threadIdx.x == 0) {
     a.chunk_sum[blockIdx.x] = total;
@@ -216,7 +259,7 @@ __global__ void __launch_bounds__(kScanThreads) batch_scan_fix(const BatchArgs a
     if (m < a.n) a.blk_off[m] += add;
   }
 }
-#endif  // AES_BATCH_REGKEYS_TU
+#endif  // !AES_BATCH_REGKEYS_TU && !AES_BATCH_LANES_TU
 
 // ------------------------------------------------------------ persistent ----
 
@@ -974,7 +1017,8 @@ __device__ void short_phase(const BatchArgs& a, const Tabs& T, const char* sb, u
       int32_t st;
       uint64_t olen;
       const uint64_t b = message_blocks(a, static_cast<uint32_t>(m0 + lane), &st, &olen);
-      if (st == AES_OK && b > 0 && b < kShortMax) {
+      const bool on_lanes = OPB == kBatchCtr && a.lane_bin != nullptr && b < kLaneMax;
+      if (st == AES_OK && b > 0 && b < kShortMax && !on_lanes) {
         nb = static_cast<uint32_t>(b);
         len = a.in_len[m0 + lane];
       }
@@ -1115,7 +1159,12 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
   __shared__ uint32_t s_span;  // next 256-block span of the current window
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // The lane kernel, launched next on the lane path, may start on SMs this
+  // grid leaves (it shares no data with this kernel and waits for its
+  // completion before it ends).
+  pdl_launch_dependents();
   const uint64_t total = a.blk_off[a.n];
+  if (total == 0 && !groups_have_work(a)) return;  // lane path: no long message, no group work
   const uint32_t tile = a.tile_blocks ? a.tile_blocks : auto_tile(total, gridDim.x, blockDim.x);
   if (warp == 0) claim_tile(a, total, tile, &s_tile[0], &s_mlo[0], &s_mhi[0]);  // overlaps the table fill
 
@@ -1189,7 +1238,8 @@ __global__ void __launch_bounds__(kRegKeys ? 512 : 1024, 1) batch_kernel(const _
     }
   }
 
-  short_phase<OPB>(a, T, sb, sb_off, reinterpret_cast<char*>(rk_all), warp, lane);
+  if (groups_have_work(a))  // on the lane path only the short messages of kLaneMax blocks or more
+    short_phase<OPB>(a, T, sb, sb_off, reinterpret_cast<char*>(rk_all), warp, lane);
 }
 
 // The persistent kernel of one build (kRegKeys: the 512-thread one).
@@ -1206,7 +1256,7 @@ cudaError_t launch_build(const BatchArgs& a, int cta, int grid, cudaStream_t s) 
 
 }  // namespace
 
-#ifdef AES_BATCH_REGKEYS_TU
+#if defined(AES_BATCH_REGKEYS_TU)
 // This translation unit (aes_batch_regkeys.cu) holds the 512-thread builds.
 cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
   switch (a.op) {
@@ -1216,17 +1266,22 @@ cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStre
   }
   return cudaErrorInvalidValue;
 }
-#else
+#elif !defined(AES_BATCH_LANES_TU)
 cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStream_t s);
 
+// Workspace layout, each part rounded up to 256 bytes: block offsets
+// (n + 1 words), chunk totals, the work counters and lane_info, then the lane
+// path's bins (n halfwords), bin counts, cursors and group-message count, and
+// order (n + 96 words).
 size_t batch_workspace_bytes(uint32_t n) {
   const size_t nchunks = (static_cast<size_t>(n) + kScanThreads * kScanItems - 1) /
                          (kScanThreads * kScanItems);
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
-  return up(8 * (static_cast<size_t>(n) + 1)) + up(8 * (nchunks > 0 ? nchunks : 1)) + 256;
+  return up(8 * (static_cast<size_t>(n) + 1)) + up(8 * (nchunks > 0 ? nchunks : 1)) + 256 +
+         up(2 * static_cast<size_t>(n)) + up(8 * kLaneBins + 4) + up(4 * (static_cast<size_t>(n) + 96));
 }
 
-void batch_bind_workspace(BatchArgs* a, void* ws) {
+void batch_bind_workspace(BatchArgs* a, void* ws, bool lanes) {
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
   const size_t nchunks = (static_cast<size_t>(a->n) + kScanThreads * kScanItems - 1) /
                          (kScanThreads * kScanItems);
@@ -1238,11 +1293,34 @@ void batch_bind_workspace(BatchArgs* a, void* ws) {
   a->tile_counter = reinterpret_cast<unsigned long long*>(p);
   a->short_counter = a->tile_counter + 1;
   a->nchunks = static_cast<uint32_t>(nchunks);
+  a->lane_bin = nullptr;
+  a->lane_hist = a->lane_cursor = a->lane_order = a->lane_info = nullptr;
+  a->lane_counter = nullptr;
+  if (!lanes) return;
+  a->lane_counter = a->tile_counter + 2;  // three counters, bytes 16..39
+  a->lane_info = reinterpret_cast<uint32_t*>(p + 64);
+  p += 256;
+  a->lane_bin = reinterpret_cast<uint16_t*>(p);
+  p += up(2 * static_cast<size_t>(a->n));
+  a->lane_hist = reinterpret_cast<uint32_t*>(p);
+  a->lane_cursor = a->lane_hist + kLaneBins;
+  p += up(8 * kLaneBins + 4);
+  a->lane_order = reinterpret_cast<uint32_t*>(p);
 }
 
+// Enqueue the pipeline.  On the lane path: the bin counts and cursors are
+// cleared first, the bin scan and scatter run before the persistent kernel
+// (which then leaves the short messages alone), and the lane kernel follows
+// it with programmatic stream serialisation, so its CTAs start on the SMs the
+// persistent kernel's CTAs leave.
 cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
+  cudaError_t e;
+  if (a.lane_bin != nullptr) {
+    e = cudaMemsetAsync(a.lane_hist, 0, (2 * kLaneBins + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
   batch_count_scan<<<a.nchunks, kScanThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.nchunks > 1) {
     batch_scan_chunks<<<1, kScanThreads, 0, s>>>(a);
@@ -1250,14 +1328,23 @@ cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s) 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (cta <= 512) return launch_batch_regkeys(a, cta, grid, s);
-  switch (a.op) {
-    case kBatchCtr: return launch_build<kBatchCtr, false>(a, cta, grid, s);
-    case kBatchEcbEnc: return launch_build<kBatchEcbEnc, false>(a, cta, grid, s);
-    case kBatchEcbDec: return launch_build<kBatchEcbDec, false>(a, cta, grid, s);
+  if (a.lane_bin != nullptr) {
+    e = launch_batch_lanes_sort(a, s);
+    if (e != cudaSuccess) return e;
   }
-  return cudaErrorInvalidValue;
+  if (cta <= 512) {
+    e = launch_batch_regkeys(a, cta, grid, s);
+  } else {
+    switch (a.op) {
+      case kBatchCtr: e = launch_build<kBatchCtr, false>(a, cta, grid, s); break;
+      case kBatchEcbEnc: e = launch_build<kBatchEcbEnc, false>(a, cta, grid, s); break;
+      case kBatchEcbDec: e = launch_build<kBatchEcbDec, false>(a, cta, grid, s); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (e != cudaSuccess || a.lane_bin == nullptr) return e;
+  return launch_batch_lanes(a, grid, s);
 }
-#endif  // AES_BATCH_REGKEYS_TU
+#endif  // AES_BATCH_REGKEYS_TU / !AES_BATCH_LANES_TU
 
 }  // namespace aesgpu

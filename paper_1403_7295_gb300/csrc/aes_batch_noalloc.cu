@@ -1,7 +1,7 @@
 // aes_batch_noalloc.cu — aes_batch_submit for callers that cannot allocate:
 // the batch pipeline's workspace (per-message block offsets, chunk totals,
-// tile counter) lives in one file-scope device array instead of a caller
-// buffer.  The work itself is the ordinary aes_batch_submit path.
+// work counters, the lane path's bins and order) lives in one file-scope
+// device array instead of a caller buffer.  The work itself is the ordinary aes_batch_submit path.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -13,13 +13,15 @@
 namespace {
 
 // Layout of the batch workspace for n messages: offsets (n + 1 words),
-// chunk totals (one word per 4096 messages), tile counter, each rounded up
-// to 256 bytes.
+// chunk totals (one word per 4096 messages), work counters, then the lane
+// path's bins (n halfwords), bin counts, cursors and a count (2 x 1536 + 1 words) and
+// order (n + 96 words), each rounded up to 256 bytes.
 constexpr size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 constexpr size_t workspace_for(size_t n) {
-  return round256(8 * (n + 1)) + round256(8 * ((n + 4095) / 4096)) + 256;
+  return round256(8 * (n + 1)) + round256(8 * ((n + 4095) / 4096)) + 256 + round256(2 * n) +
+         round256(8 * 1536 + 4) + round256(4 * (n + 96));
 }
-constexpr size_t kScratchBytes = workspace_for(AES_BATCH_NOALLOC_MAX_MSGS);  // 525,056 bytes
+constexpr size_t kScratchBytes = workspace_for(AES_BATCH_NOALLOC_MAX_MSGS);  // 931,328 bytes
 
 // Held by every device that loads the library, for the life of the process.
 static __device__ __align__(256) unsigned char g_batch_scratch[kScratchBytes];
@@ -70,7 +72,7 @@ extern "C" aes_status aes_batch_submit_noalloc(const aes_batch* b, void* stream)
   void* ws = nullptr;
   const aes_status s = scratch_for_current_device(&ws);
   if (s != AES_OK) return s;
-  // No counter needs clearing here: the pipeline's first kernel resets the
-  // tile counter and rewrites every offset the later kernels read.
+  // Nothing needs clearing here: the pipeline itself resets the work
+  // counters and bin counts and rewrites every offset the later kernels read.
   return aes_batch_submit_ex(b, ws, kScratchBytes, stream, nullptr);
 }
