@@ -691,7 +691,7 @@ def batched_arm(torch, A):
         "plain_mix_gbps": round(mix, 1), "ratio_vs_plain": round(gbps / mix, 4),
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks,
                    "short_path": SHORT_PATH_NAMES[cfg.short_path]},
-        "kernels_per_batch": 4 if cfg.short_path != B.SHORT_LANES else 6, "graph": True,
+        "kernels_per_batch": 2 if cfg.short_path != B.SHORT_LANES else 4, "graph": True,
     }
     # the same messages as ECB + PKCS#7, encrypt then decrypt, against the ECB mix
     ecb_rates = {}
@@ -758,7 +758,7 @@ def batched_arm(torch, A):
         "per_batch_device_keys": {k: st_small[k] for k in ("median_ms", "p99_ms", "paper_mean_ms")},
         "launch": {"cta_threads": cfg.cta_threads, "tile_blocks": cfg.tile_blocks,
                    "short_path": SHORT_PATH_NAMES[cfg.short_path]},
-        "kernels_per_batch": 4 if cfg.short_path != B.SHORT_LANES else 6,
+        "kernels_per_batch": 2 if cfg.short_path != B.SHORT_LANES else 4,
         "launch_preexpanded": {"cta_threads": cfg2.cta_threads, "tile_blocks": cfg2.tile_blocks,
                                "short_path": SHORT_PATH_NAMES[cfg2.short_path]},
     }

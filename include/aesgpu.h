@@ -227,7 +227,7 @@ typedef struct aes_batch {
                                     consecutive messages, their round keys in shared memory */
 #define AES_BATCH_SHORT_LANES 2  /* CTR only: one lane per message of fewer than 128 blocks, its
                                     round keys in registers; those messages are first sorted by key
-                                    size and length (a memset and one more launch), then a kernel of
+                                    size and length (one more launch), then a kernel of
                                     their own runs them after the persistent kernel, which keeps the
                                     longer short messages (other ops: AES_ERR_ARG).  Faster on large
                                     batches of packet-sized messages, slower on small batches: a lane
@@ -248,11 +248,11 @@ typedef struct aes_batch_config {
 /* Bytes of device workspace aes_batch_submit needs for n_msgs messages. */
 size_t aes_batch_workspace_size(uint32_t n_msgs);
 
-/* Enqueue one batch on `stream` (4 kernel launches: count+scan, chunk scan,
- * offset fix, persistent cipher kernel; on the lane path of short CTR
- * messages also a memset of the bin counts, the scatter into bin order and
- * the lane kernel; no allocation, no host sync, so the call can be captured
- * into a CUDA graph and replayed).  d_workspace: device,
+/* Enqueue one batch on `stream` (a memset of the work counters and 2 kernel
+ * launches: count + scan, persistent cipher kernel; on the lane path of short
+ * CTR messages also the scatter into bin order and the lane kernel; no
+ * allocation, no host sync, so the call can be captured into a CUDA graph
+ * and replayed).  d_workspace: device,
  * 256-byte aligned, at least aes_batch_workspace_size(n_msgs) bytes; its
  * contents need no initialisation.  Per-message failures (bad key size,
  * unaligned offset, bad ECB length or padding) are reported in status[m]

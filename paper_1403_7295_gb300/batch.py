@@ -183,7 +183,7 @@ class Batch:
         aes_batch_submit(self.desc, self.workspace, stream, config)
         return self
 
-    # -- CUDA graph: the four launches of one submit, captured once, replayed
+    # -- CUDA graph: the memset and launches of one submit, captured once, replayed
     def capture(self, config: AesBatchConfig | None = None):
         import torch
 

@@ -3,17 +3,18 @@
 // §IV.B with chunks = messages, mapped onto blocks of a GPU grid).
 //
 // Pipeline on the caller's stream:
+//   0. a memset of the work counters (and, on the lane path of short CTR
+//      messages, the bin counts).
 //   1. batch_count_scan  per message: validate, count 16-byte blocks
 //      (CTR ceil(len/16); ECB+PKCS#7 encrypt floor(len/16)+1; decrypt len/16),
 //      write status/out_len, exclusive-scan the counts of long messages
-//      (kShortMax blocks or more) inside chunks of 4096 messages; reset the
-//      work counters.
-//   2. batch_scan_chunks one CTA scans the chunk totals and writes the grand total.
-//   3. batch_scan_fix    adds each chunk's offset: blk_off[m] = first block of m
-//      in the long-message block space.
-//   4. batch_kernel      persistent CTAs.  Long messages: the CTA claims tiles of
+//      (kShortMax blocks or more) inside chunks of 4096 messages.  The last
+//      CTA to finish scans the chunk totals into chunk offsets and writes the
+//      grand total: blk_start(m) = the chunk offset + m's offset in its chunk.
+//   2. (lane path) the scatter of short CTR messages into bin order.
+//   3. batch_kernel      persistent CTAs.  Long messages: the CTA claims tiles of
 //      `tile_blocks` blocks of the long-message space with an atomic counter,
-//      finds the tile's messages by a 32-way warp search over blk_off, expands
+//      finds the tile's messages by a 32-way warp search over blk_start, expands
 //      their keys on the device into shared memory (one thread per message,
 //      FIPS-197 §5.2; the equivalent inverse schedule for ECB decryption), and
 //      its warps run the T-table rounds of aes_ttable.cuh with round keys read
@@ -195,18 +196,45 @@ __device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* sh,
   return before + x - v;
 }
 
+// Messages per chunk of the count kernel (one CTA).
+constexpr uint32_t kChunkMsgs = kScanThreads * kScanItems;
+
+// First block of message m in the long-message space (m == n: the total).
+__device__ __forceinline__ uint64_t blk_start(const BatchArgs& a, uint64_t m) {
+  return m >= a.n ? a.blk_off[a.n] : a.blk_off[m] + a.chunk_sum[m / kChunkMsgs];
+}
+
 #if !defined(AES_BATCH_REGKEYS_TU) && !defined(AES_BATCH_LANES_TU)  // run from aes_batch.cu's entry point only
-__global__ void __launch_bounds__(kScanThreads, 1) batch_count_scan(const BatchArgs a) {
+// Lane path, by the count kernel's last CTA: each bin's first position in
+// lane_order (each key-size class from a multiple of 32), written over the
+// bin counts; the class gaps filled with kLaneNoMsg; the chunk range of each
+// class.  Threads 512.. add nothing to the scans.
+__device__ void lane_bin_starts(const BatchArgs& a, uint64_t* sh) {
+  uint64_t base = 0;  // first position of the class
+  for (uint32_t c = 0; c < 3; ++c) {
+    const uint32_t b = c * 512 + threadIdx.x;
+    uint64_t total;
+    const uint64_t ex = cta_exclusive_scan(threadIdx.x < 512 ? __ldcg(a.lane_hist + b) : 0, sh, &total);
+    if (threadIdx.x < 512) a.lane_hist[b] = static_cast<uint32_t>(base + ex);
+    const uint64_t end = base + total, next = (end + 31) & ~static_cast<uint64_t>(31);
+    if (threadIdx.x < next - end) a.lane_order[end + threadIdx.x] = kLaneNoMsg;
+    if (threadIdx.x == 0) a.lane_info[1 + c] = static_cast<uint32_t>(base / 32);
+    base = next;
+  }
+  if (threadIdx.x == 0) a.lane_info[0] = a.lane_info[4] = static_cast<uint32_t>(base / 32);
+}
+
+__global__ void __launch_bounds__(kScanThreads, 2) batch_count_scan(const BatchArgs a) {
   __shared__ uint64_t sh[64];
   __shared__ uint32_t lane_hist[kLaneBins + 1];  // the lane path's bin counts of this CTA's messages, and
                                                  // its short messages left to the per-warp groups
+  __shared__ bool s_last;
   const bool lanes = a.lane_bin != nullptr;
   if (lanes) {
     for (uint32_t i = threadIdx.x; i <= kLaneBins; i += blockDim.x) lane_hist[i] = 0;
     __syncthreads();
   }
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems +
-                        static_cast<uint64_t>(threadIdx.x) * kScanItems;
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kChunkMsgs + static_cast<uint64_t>(threadIdx.x) * kScanItems;
   uint64_t cnt[kScanItems], sum = 0;
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k) {
@@ -219,7 +247,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) batch_count_scan(const BatchA
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k) {
     const uint64_t m = base + k;
-    if (m < a.n) a.blk_off[m] = run;
+    if (m < a.n) a.blk_off[m] = run;  // from the chunk's first block
     run += cnt[k];
   }
   if (lanes) {
@@ -227,51 +255,40 @@ __global__ void __launch_bounds__(kScanThreads, 1) batch_count_scan(const BatchA
       if (lane_hist[i] != 0) atomicAdd(a.lane_hist + i, lane_hist[i]);
     if (threadIdx.x == 0 && lane_hist[kLaneBins] != 0) atomicAdd(a.lane_cursor + kLaneBins, lane_hist[kLaneBins]);
   }
-  if (threadIdx.x == 0) {
-    a.chunk_sum[blockIdx.x] = total;
-    if (gridDim.x == 1) a.blk_off[a.n] = total;
-    if (blockIdx.x == 0) {
-      *a.tile_counter = 0;
-      *a.short_counter = 0;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) batch_scan_chunks(const BatchArgs a) {
-  __shared__ uint64_t sh[64];
+  if (threadIdx.x == 0) a.chunk_sum[blockIdx.x] = total;
+  // The last CTA to finish turns the chunk totals into chunk offsets and
+  // writes the grand total (and, on the lane path, the bin starts).
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.scan_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   uint64_t carry = 0;
-  for (uint32_t c0 = 0; c0 < a.nchunks; c0 += kScanThreads) {
+  for (uint32_t c0 = 0; c0 < a.nchunks; c0 += blockDim.x) {
     const uint32_t c = c0 + threadIdx.x;
-    const uint64_t v = c < a.nchunks ? a.chunk_sum[c] : 0;
-    uint64_t total;
-    const uint64_t ex = cta_exclusive_scan(v, sh, &total);
+    const uint64_t v = c < a.nchunks ? __ldcg(a.chunk_sum + c) : 0;  // other CTAs' totals, from L2
+    uint64_t t;
+    const uint64_t ex = cta_exclusive_scan(v, sh, &t);
     if (c < a.nchunks) a.chunk_sum[c] = carry + ex;
-    carry += total;
+    carry += t;
   }
   if (threadIdx.x == 0) a.blk_off[a.n] = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads) batch_scan_fix(const BatchArgs a) {
-  const uint64_t add = a.chunk_sum[blockIdx.x];
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems;
-  for (uint32_t k = threadIdx.x; k < kScanThreads * kScanItems; k += blockDim.x) {
-    const uint64_t m = base + k;
-    if (m < a.n) a.blk_off[m] += add;
-  }
+  if (lanes) lane_bin_starts(a, sh);
 }
 #endif  // !AES_BATCH_REGKEYS_TU && !AES_BATCH_LANES_TU
 
 // ------------------------------------------------------------ persistent ----
 
-// Largest m in [0, n) with blk_off[m] <= g (blk_off non-decreasing, blk_off[0] = 0),
+// Largest m in [0, n) with blk_start(m) <= g (non-decreasing, blk_start(0) = 0),
 // by a 32-way search: each step narrows the range 32-fold.  Whole warp calls.
-__device__ __forceinline__ uint32_t warp_find(const uint64_t* blk_off, uint32_t n, uint64_t g) {
+__device__ __forceinline__ uint32_t warp_find(const BatchArgs& a, uint32_t n, uint64_t g) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t lo = 0, hi = n;
   while (hi - lo > 1) {
     const uint32_t step = (hi - lo + 31) / 32;
     const uint64_t idx = static_cast<uint64_t>(lo) + static_cast<uint64_t>(lane) * step;
-    const bool ok = lane == 0 || (idx < hi && blk_off[idx] <= g);
+    const bool ok = lane == 0 || (idx < hi && blk_start(a, idx) <= g);
     const uint32_t mask = __ballot_sync(0xffffffffu, ok);
     const uint32_t last = 31 - __clz(mask);
     lo = lo + last * step;
@@ -524,7 +541,7 @@ __device__ void fill_slot(const BatchArgs& a, const Tabs& T, const char* sb, uin
 template <int OPB>
 __device__ __forceinline__ void load_slot(const BatchArgs& a, const Tabs& T, const char* sb,
                                           uint32_t sb_off, uint32_t m, Slot& sl, uint32_t* rk) {
-  fill_slot<OPB>(a, T, sb, sb_off, m, a.blk_off[m], a.blk_off[m + 1], sl, rk);
+  fill_slot<OPB>(a, T, sb, sb_off, m, blk_start(a, m), blk_start(a, m + 1ull), sl, rk);
 }
 
 // The message a thread is working in, cached in registers and rebased to the
@@ -859,8 +876,8 @@ __device__ __forceinline__ void claim_tile(const BatchArgs& a, uint64_t total, u
   const uint64_t t0 = t * tile;
   uint32_t mlo = 0, mhi = 0;
   if (t0 < total) {
-    mlo = warp_find(a.blk_off, a.n, t0);
-    mhi = warp_find(a.blk_off, a.n, min(t0 + tile, total) - 1);
+    mlo = warp_find(a, a.n, t0);
+    mhi = warp_find(a, a.n, min(t0 + tile, total) - 1);
   }
   if (lane == 0) {
     *s_tile = t;
@@ -1270,64 +1287,59 @@ cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStre
 cudaError_t launch_batch_regkeys(const BatchArgs& a, int cta, int grid, cudaStream_t s);
 
 // Workspace layout, each part rounded up to 256 bytes: block offsets
-// (n + 1 words), chunk totals, the work counters and lane_info, then the lane
-// path's bins (n halfwords), bin counts, cursors and group-message count, and
-// order (n + 96 words).
+// (n + 1 words), chunk totals, the work counters and lane_info, the lane
+// path's bin counts, cursors and group-message count (cleared together with
+// the counters by one memset), then its bins (n halfwords) and order
+// (n + 96 words).
+constexpr size_t kCounterBytes = 256;
+constexpr size_t kLaneCountBytes = (8 * kLaneBins + 4 + 255) & ~static_cast<size_t>(255);
+
 size_t batch_workspace_bytes(uint32_t n) {
-  const size_t nchunks = (static_cast<size_t>(n) + kScanThreads * kScanItems - 1) /
-                         (kScanThreads * kScanItems);
+  const size_t nchunks = (static_cast<size_t>(n) + kChunkMsgs - 1) / kChunkMsgs;
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
-  return up(8 * (static_cast<size_t>(n) + 1)) + up(8 * (nchunks > 0 ? nchunks : 1)) + 256 +
-         up(2 * static_cast<size_t>(n)) + up(8 * kLaneBins + 4) + up(4 * (static_cast<size_t>(n) + 96));
+  return up(8 * (static_cast<size_t>(n) + 1)) + up(8 * (nchunks > 0 ? nchunks : 1)) + kCounterBytes +
+         kLaneCountBytes + up(2 * static_cast<size_t>(n)) + up(4 * (static_cast<size_t>(n) + 96));
 }
 
 void batch_bind_workspace(BatchArgs* a, void* ws, bool lanes) {
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
-  const size_t nchunks = (static_cast<size_t>(a->n) + kScanThreads * kScanItems - 1) /
-                         (kScanThreads * kScanItems);
+  const size_t nchunks = (static_cast<size_t>(a->n) + kChunkMsgs - 1) / kChunkMsgs;
   char* p = static_cast<char*>(ws);
   a->blk_off = reinterpret_cast<uint64_t*>(p);
   p += up(8 * (static_cast<size_t>(a->n) + 1));
   a->chunk_sum = reinterpret_cast<uint64_t*>(p);
   p += up(8 * (nchunks > 0 ? nchunks : 1));
-  a->tile_counter = reinterpret_cast<unsigned long long*>(p);
-  a->short_counter = a->tile_counter + 1;
+  a->tile_counter = reinterpret_cast<unsigned long long*>(p);  // bytes 0..7 of the counters
+  a->short_counter = a->tile_counter + 1;                       // 8..15
+  a->scan_done = reinterpret_cast<unsigned int*>(p + 48);       // 48..51
   a->nchunks = static_cast<uint32_t>(nchunks);
   a->lane_bin = nullptr;
   a->lane_hist = a->lane_cursor = a->lane_order = a->lane_info = nullptr;
   a->lane_counter = nullptr;
   if (!lanes) return;
-  a->lane_counter = a->tile_counter + 2;  // three counters, bytes 16..39
-  a->lane_info = reinterpret_cast<uint32_t*>(p + 64);
-  p += 256;
-  a->lane_bin = reinterpret_cast<uint16_t*>(p);
-  p += up(2 * static_cast<size_t>(a->n));
+  a->lane_counter = a->tile_counter + 2;  // three counters, 16..39
+  a->lane_info = reinterpret_cast<uint32_t*>(p + 64);  // 64..83
+  p += kCounterBytes;
   a->lane_hist = reinterpret_cast<uint32_t*>(p);
   a->lane_cursor = a->lane_hist + kLaneBins;
-  p += up(8 * kLaneBins + 4);
+  p += kLaneCountBytes;
+  a->lane_bin = reinterpret_cast<uint16_t*>(p);
+  p += up(2 * static_cast<size_t>(a->n));
   a->lane_order = reinterpret_cast<uint32_t*>(p);
 }
 
-// Enqueue the pipeline.  On the lane path: the bin counts and cursors are
-// cleared first, the bin scan and scatter run before the persistent kernel
-// (which then leaves the short messages alone), and the lane kernel follows
-// it with programmatic stream serialisation, so its CTAs start on the SMs the
-// persistent kernel's CTAs leave.
+// Enqueue the pipeline: the counters (and on the lane path the bin counts)
+// cleared, the count kernel (whose last CTA finishes the scans), on the lane
+// path the scatter into bin order, the persistent kernel (which then leaves
+// the short messages of fewer than kLaneMax blocks alone), and on the lane
+// path the lane kernel, launched with programmatic stream serialisation so
+// its CTAs start on the SMs the persistent kernel's CTAs leave.
 cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s) {
-  cudaError_t e;
-  if (a.lane_bin != nullptr) {
-    e = cudaMemsetAsync(a.lane_hist, 0, (2 * kLaneBins + 1) * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = cudaMemsetAsync(a.tile_counter, 0, kCounterBytes + (a.lane_bin != nullptr ? kLaneCountBytes : 0), s);
+  if (e != cudaSuccess) return e;
   batch_count_scan<<<a.nchunks, kScanThreads, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.nchunks > 1) {
-    batch_scan_chunks<<<1, kScanThreads, 0, s>>>(a);
-    batch_scan_fix<<<a.nchunks, kScanThreads, 0, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   if (a.lane_bin != nullptr) {
     e = launch_batch_lanes_sort(a, s);
     if (e != cudaSuccess) return e;

@@ -41,10 +41,12 @@ struct BatchArgs {
   uint64_t* out_len;
   int32_t* status;
   // workspace
-  uint64_t* blk_off;    // [n + 1] first global block of each message; [n] = total
+  uint64_t* blk_off;    // [n + 1] first block of each message in the long-message space, counted from
+                        // its chunk's first block (blk_start adds the chunk offset); [n] = total
   uint64_t* chunk_sum;  // [nchunks] per-chunk totals, then chunk offsets
   unsigned long long* tile_counter;   // next tile of the long-message block space
   unsigned long long* short_counter;  // next group of messages for the short-message phase
+  unsigned int* scan_done;            // count-kernel CTAs finished (the last one scans the chunk totals)
   uint32_t nchunks;
   // The lane path of short CTR messages (one lane per message); all null when
   // the persistent kernel's per-warp groups run them instead.
@@ -68,6 +70,8 @@ cudaError_t launch_batch(const BatchArgs& a, int cta, int grid, cudaStream_t s);
 
 // The lane path's steps (aes_batch_lanes.cu): the scatter into bin order,
 // enqueued before the persistent kernel, then the lane kernel, enqueued after it.
+// (The bin starts, gaps and chunk ranges are computed by the count kernel's
+// last CTA.)
 cudaError_t launch_batch_lanes_sort(const BatchArgs& a, cudaStream_t s);
 cudaError_t launch_batch_lanes(const BatchArgs& a, int grid, cudaStream_t s);
 // Bounded waits of the lane kernel that gave up since the last call; resets the count.

@@ -19,12 +19,12 @@
 //
 // Steps (after aes_batch.cu's count kernel has binned every accepted short
 // message by (key-size class, 511 - blocks)):
-//   1. lanes_scatter  per message chunk of the count kernel: every CTA scans
-//                     the bin counts (each key-size class starting on a
-//                     multiple of 32, bins longest first) and places its
+//   1. lanes_scatter  per message chunk of the count kernel: places its
 //                     messages with a per-CTA rank and one global cursor add
-//                     per bin; CTA 0 also fills the class gaps with
-//                     kLaneNoMsg and resets the chunk counters.
+//                     per bin, from the bin starts the count kernel's last
+//                     CTA computed (each key-size class from a multiple of
+//                     32, bins longest first, the class gaps filled with
+//                     kLaneNoMsg).
 //   2. batch_lanes_kernel  persistent, 512 threads (128 registers, room for
 //                     an AES-256 schedule).  A warp claims 32 consecutive
 //                     positions (one key-size class, nearly equal lengths) and
@@ -78,32 +78,12 @@ __device__ unsigned int g_lane_timeouts = 0;
 // ------------------------------------------------------------------ sort ----
 
 // The count kernel's partition: kScanItems consecutive messages per thread.
+// lane_hist holds each bin's first position (the count kernel's last CTA).
 __global__ void __launch_bounds__(kScanThreads) lanes_scatter(const BatchArgs a) {
-  __shared__ uint64_t sh[64];
-  __shared__ uint32_t start[kLaneBins], cnt[kLaneBins], first[kLaneBins];
+  __shared__ uint32_t cnt[kLaneBins], first[kLaneBins];
   for (uint32_t i = threadIdx.x; i < kLaneBins; i += blockDim.x) cnt[i] = 0;
-  // bin start positions: per class an exclusive scan of its 512 bins, the
-  // class starting on a multiple of 32 (threads 512.. add nothing)
-  uint64_t base = 0;
-  for (uint32_t c = 0; c < 3; ++c) {
-    const uint32_t b = c * 512 + threadIdx.x;
-    uint64_t total;
-    const uint64_t ex = cta_exclusive_scan(threadIdx.x < 512 ? a.lane_hist[b] : 0, sh, &total);
-    if (threadIdx.x < 512) start[b] = static_cast<uint32_t>(base + ex);
-    const uint64_t end = base + total, next = (end + 31) & ~static_cast<uint64_t>(31);
-    if (blockIdx.x == 0) {
-      if (threadIdx.x < next - end) a.lane_order[end + threadIdx.x] = kLaneNoMsg;
-      if (threadIdx.x == 0) {
-        a.lane_info[1 + c] = static_cast<uint32_t>(base / 32);
-        a.lane_counter[c] = 0;
-      }
-    }
-    base = next;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.lane_info[0] = a.lane_info[4] = static_cast<uint32_t>(base / 32);
   __syncthreads();
-  const uint64_t m0 = static_cast<uint64_t>(blockIdx.x) * kScanThreads * kScanItems +
-                      static_cast<uint64_t>(threadIdx.x) * kScanItems;
+  const uint64_t m0 = static_cast<uint64_t>(blockIdx.x) * kChunkMsgs + static_cast<uint64_t>(threadIdx.x) * kScanItems;
   uint32_t bin[kScanItems], rank[kScanItems];
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k) {
@@ -112,7 +92,7 @@ __global__ void __launch_bounds__(kScanThreads) lanes_scatter(const BatchArgs a)
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kLaneBins; i += blockDim.x)
-    if (cnt[i] != 0) first[i] = start[i] + atomicAdd(a.lane_cursor + i, cnt[i]);
+    if (cnt[i] != 0) first[i] = a.lane_hist[i] + atomicAdd(a.lane_cursor + i, cnt[i]);
   __syncthreads();
 #pragma unroll
   for (uint32_t k = 0; k < kScanItems; ++k)
