@@ -228,3 +228,33 @@ def test_xts_key_sizes_refused_before_any_gpu_work(lib):
     for d, t in ((192, 192), (128, 256), (256, 128), (192, 128), (128, 192)):
         for fn in (lib.aes_xts_encrypt, lib.aes_xts_decrypt):
             assert fn(ctypes.byref(ks[d]), ctypes.byref(ks[t]), 0, 512, p, p, 4096, None) == 2
+
+
+def test_batch_workspace_layout_and_short_path_refusals(lib):
+    """aes_batch_workspace_size is the sum of its parts, each rounded up to
+    256 bytes: block offsets (n + 1 words), chunk totals (one per 4096
+    messages), the work counters, the lane path's bin counts and cursors
+    (2 x 1536 + 1 words), its bins (n halfwords) and order (n + 96 words); the
+    allocation-free call's scratch is that size at its cap of 65,536
+    messages.  A short_path outside AES_BATCH_SHORT_*, or the lane path for
+    an ECB batch, is refused before any CUDA call."""
+    from paper_1403_7295_gb300 import batch as BT
+
+    L = BT._declare()
+    up = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    for n in (1, 4095, 4096, 4097, 65536, 1_000_000):
+        want = (up(8 * (n + 1)) + up(8 * -(-n // 4096)) + 256 + up(8 * 1536 + 4) + up(2 * n)
+                + up(4 * (n + 96)))
+        assert L.aes_batch_workspace_size(n) == want, n
+    assert L.aes_batch_workspace_size(65536) == 931_328
+    base = 1 << 20  # never dereferenced: every case below fails validation first
+    d = BT.AesBatch()
+    d.n_msgs, d.in_, d.out = 4, base, base + (1 << 16)
+    d.in_off, d.in_len, d.out_off = base + 4096, base + 8192, base + 12288
+    d.keys, d.key_bits, d.iv = base + 16384, base + 20480, base + 24576
+    ws = base + (1 << 17)
+    for op, path in ((BT.BATCH_CTR, 3), (BT.BATCH_CTR, -1), (BT.BATCH_ECB_PKCS7_ENCRYPT, BT.SHORT_LANES),
+                     (BT.BATCH_ECB_PKCS7_DECRYPT, BT.SHORT_LANES)):
+        d.op = op
+        cfg = BT.AesBatchConfig(1024, 0, 152, path)
+        assert L.aes_batch_submit_ex(ctypes.byref(d), ws, 1 << 30, None, ctypes.byref(cfg)) == 1, (op, path)
