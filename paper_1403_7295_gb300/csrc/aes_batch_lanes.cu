@@ -27,17 +27,17 @@
 //                     kLaneNoMsg).
 //   2. batch_lanes_kernel  persistent, 512 threads (128 registers, room for
 //                     an AES-256 schedule).  A warp claims 32 consecutive
-//                     positions (one key-size class, nearly equal lengths) and
-//                     walks the messages in stages of 8 blocks: each lane
+//                     positions (one key-size class, nearly equal lengths)
+//                     and walks the messages in stages of 8 blocks: each lane
 //                     copies its message's next 8 whole blocks into its own
 //                     shared-memory slot with one TMA bulk copy, computes the
 //                     keystream two blocks at a time with the counter-run
 //                     caching of the single-buffer kernel (rounds 1-2 mostly
 //                     precomputed per run of 256 counters), and stores each
 //                     result block with a plain 128-bit streaming store.  A
-//                     ragged last block (without the padded flags) is read and
-//                     written byte-exactly instead.  While a chunk runs, the
-//                     warp claims the next one, looks up its messages and
+//                     ragged last block (without the padded flags) is read
+//                     and written byte-exactly instead.  While a chunk runs,
+//                     the warp claims the next one, looks up its messages and
 //                     prefetches their descriptors into L2.
 //
 // Measured choices (packet-sized batch, 1M messages of 16-1500 bytes):
